@@ -1,0 +1,326 @@
+"""Benchmark: gate throughput of the state-vector engine on GB300.
+
+Workload (one step): the two n=30 complex128 circuits of the large-state
+configuration, applied gate by gate through qc_apply_circuit from a seeded
+basis state -- the QFT circuit of QCLAB++ Fig. 1 (480 gates: 30 H, 435
+controlled phases, 15 SWAP) and a depth-40 brickwork circuit (1200 Haar U(2),
+580 CNOT).  `value` = gates per second over both circuits (device time, inputs
+resident in HBM; the 17.2 GB state is far larger than the 129 MB L2, so no
+flush is needed between launches).
+
+Extra keys: `roofline` of the dominant kernel (dense 1-qubit sweep) from the
+per-launch CUDA-event times recorded on the launching stream; `e2e` through the
+C ABI with pinned host buffers (host->device state copy, circuits, device->host
+copy of the final state); `cpu_baseline` = the FP64 CPU oracle timed on a
+bounded sample on this machine's host cores; `clocks` sampled with nvidia-smi
+during the timed region.  `--impl reference` times the oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2303_00123_gb300 import circuits as C  # noqa: E402
+
+N_QUBITS = 30
+BRICK_DEPTH = 40
+SEED_BASIS = 1000
+SEED_BRICK = 1001
+HBM_FALLBACK = 6800.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return HBM_FALLBACK, "fallback"
+
+
+def workload():
+    rng = np.random.default_rng(SEED_BASIS)
+    x = int(rng.integers(0, 1 << N_QUBITS))
+    return x, C.qft(N_QUBITS), C.brickwork(N_QUBITS, BRICK_DEPTH, seed=SEED_BRICK)
+
+
+def algorithmic_bytes(g, n, elem):
+    """Read+write bytes a gate sweep must move (what it changes, nothing else)."""
+    N = 1 << n
+    name = g.name.upper()
+    nc = len(g.controls)
+    frac = 1.0 / (1 << nc)
+    if name == "SWAP":
+        return 2 * N * elem * 0.5 * frac
+    if name in ("X",):
+        return 2 * N * elem * frac
+    if name in ("Z", "S", "SDG", "T", "TDG", "P"):
+        return 2 * N * elem * 0.5 * frac
+    return 2 * N * elem * frac
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    for f in ("qc_common.cuh", "qc_gates.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2303_00123_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dense 1-qubit kernel from the committed
+    ncu summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "dense1q_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("src_sha") != kernel_sources_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(n_gates_each=6):
+    """Oracle (FP64 C, OpenMP) on the first gates of both circuits at n=30."""
+    from oracle import oracle as O
+    x, qft, brick = workload()
+    sample = qft[:n_gates_each] + brick[:n_gates_each]
+    psi = O.basis_state(N_QUBITS, x)
+    t0 = time.perf_counter()
+    for g in sample:
+        O.apply_gate(psi, N_QUBITS, g)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": len(sample) / dt, "unit": "gates/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d gates of the QFT and of the brickwork circuit at n=%d complex128 "
+                      "(%d gates, %.1f s)" % (n_gates_each, N_QUBITS, len(sample), dt)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2303_00123_gb300 import qcgb300 as q
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = N_QUBITS
+    x, qft, brick = workload()
+    gates_per_step = len(qft) + len(brick)
+    t = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+    st = q.State.from_tensor(t)
+    st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
+    stream = torch.cuda.Stream()
+    st.set_stream(stream)
+    elem = 16
+
+    dense_ms, dense_bytes = [], 0.0
+    launches = 0
+
+    def step(record):
+        nonlocal launches, dense_bytes
+        for circ in (qft, brick):
+            st.set_basis(x)
+            nl, ms = st.apply_circuit(circ, fuse_k=args.fuse, time_gates=record)
+            launches += nl
+            if record and args.fuse == 0:
+                for g, m in zip(circ, ms):
+                    if g.name.upper() == "U" and not g.controls:
+                        dense_ms.append(m)
+                        dense_bytes += algorithmic_bytes(g, n, elem)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    launches = 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+        dist.barrier()
+    total_gates = gates_per_step * args.steps * world
+    value = total_gates / elapsed
+
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if dense_ms:
+        per_launch_bytes = dense_bytes / len(dense_ms)
+        avg_ms = float(np.mean(dense_ms))
+        achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                "kernel": "k_dense (1-qubit Haar U(2), complex128, %s)" % args.arith,
+                "peak_kind": peak_kind + " (copy bandwidth, MEASURED_PEAKS.json)",
+                "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": round(avg_ms, 4),
+                "launches": len(dense_ms)}
+
+    # e2e through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(1 << n, dtype=torch.complex128, pin_memory=True)
+        host.zero_()
+        host[x] = 1.0
+        hnp = host.numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for circ in (qft, brick):
+                q.lib.qc_state_copy_from_host(st.handle, q.ctypes.c_void_p(hnp.ctypes.data))
+                st.apply_circuit(circ, fuse_k=args.fuse)
+                st.to_numpy(out=hnp)        # device->host copy of the final state (synchronises)
+                hnp[:] = 0
+                hnp[x] = 1.0
+        e2e_s = time.perf_counter() - t0
+        bi = 2 * (1 << n) * elem
+        e2e = {"value": gates_per_step * args.steps * world / e2e_s, "unit": "gates/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi}
+
+    line = {
+        "metric": "gates/s at n=30 complex128 (QFT 480 + brickwork depth-40 1780 gates, unfused)",
+        "value": round(value, 3), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed / args.steps * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128-" + args.arith, "data": "synthetic",
+        "config": {"workload": "configs[1]: n=30 complex128 QFT (seeded basis state) + brickwork depth 40 (Haar U(2) "
+                               "layers + CNOT pairs), gate by gate", "n": n, "gates_per_step": gates_per_step,
+                   "fuse_k": args.fuse, "arith": args.arith, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (17.2 GB state vs 129 MB)"},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    st.free()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    x, qft, brick = workload()
+    sample = qft[:3] + brick[:3]
+    psi = O.basis_state(N_QUBITS, x)
+    for _ in range(args.warmup):
+        O.apply_gate(psi, N_QUBITS, sample[0])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for g in sample:
+            O.apply_gate(psi, N_QUBITS, g)
+    dt = time.perf_counter() - t0
+    value = len(sample) * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cpu = {"value": value, "unit": "gates/s", "cores": cores, "kind": "oracle",
+           "sample": "each step: first 3 gates of the QFT and of the brickwork circuit at n=30 complex128"}
+    print(json.dumps({
+        "impl": "reference", "metric": "gates/s at n=30 complex128 (QFT 480 + brickwork depth-40 1780 gates, unfused)",
+        "value": round(value, 4), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "configs[1] sample, FP64 CPU oracle", "n": N_QUBITS},
+        "cpu_baseline": cpu, "e2e": {"value": round(value, 4), "unit": "gates/s", "h2d_bytes_per_step": 0,
+                                     "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--arith", default="f32x2", choices=["f32x2", "native"])
+    ap.add_argument("--fuse", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * qcgb300.h -- C ABI of the GB300 (sm_103a) state-vector gate engine.
+ *
+ * The library applies quantum gates to a dense state |phi> in C^(2^n) held in
+ * device memory, following QCLAB++ (arXiv 2303.00123), Sec. 2:
+ *
+ *   |psi> = (I_l (x) U (x) I_r) |phi>                              (Eq. (1))
+ *
+ * Qubit numbering is Definition 1 (big-endian): qubit 0 is the most
+ * significant bit of a basis index j, so qubit q has stride 2^(n-q-1).
+ * Amplitudes are stored interleaved (re, im): complex<float> (QC_C64, 8 bytes)
+ * or complex<double> (QC_C128, 16 bytes), index j at byte offset j*E.
+ * Every update is in place (the paper's kernels overwrite their input, Fig. 4).
+ *
+ * Matrices are always passed by the caller as host arrays of FP64 (re, im)
+ * pairs, row-major, and are copied during the call (the caller may free or
+ * reuse them on return).  For a gate on target qubits (t_0, ..., t_{k-1}) the
+ * row/column index of U is the big-endian number formed by the target bits,
+ * t_0 being the most significant -- the order that Eq. (1) fixes for a gate
+ * on adjacent qubits, kept for any placement (Sec. 2.3 remarks that the
+ * 2-qubit algorithm also covers non-adjacent qubits, Fig. 1(e)).
+ *
+ * Execution: every apply call only enqueues kernels on the state's stream
+ * (qc_set_stream; default: the legacy default stream) and returns.  Calls that
+ * return host data (qc_expect, qc_state_copy_to_host, qc_apply_circuit with
+ * per-gate timing) synchronise that stream.  There is no CPU fallback: when no
+ * CUDA device is usable every call returns QC_ERR_CUDA.
+ *
+ * Errors: every int-returning call returns QC_OK (0) or a negative QC_ERR_*
+ * code and then leaves a message in qc_last_error() (thread-local).  A call
+ * that fails argument validation has no effect.  Asynchronous kernel faults
+ * surface as QC_ERR_CUDA on a later synchronising call.
+ *
+ * Thread safety: distinct states may be used from distinct threads; a single
+ * state must not be used concurrently.
+ */
+#ifndef QCGB300_H
+#define QCGB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define QC_OK 0
+#define QC_ERR_ARG (-1)         /* invalid argument (qubit out of range, duplicate qubit, ...) */
+#define QC_ERR_OOM (-2)         /* device allocation failed */
+#define QC_ERR_CUDA (-3)        /* a CUDA runtime call failed / no device */
+#define QC_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define QC_ERR_UNSUPPORTED (-5) /* valid request that this build does not implement */
+
+/* ---- element types ------------------------------------------------------ */
+typedef enum { QC_C64 = 0, QC_C128 = 1 } qc_dtype;
+
+/*
+ * Arithmetic used for QC_C128 states.  GB300 executes FP64 at about 1/64 of
+ * its FP32 rate, so a dense complex128 gate sweep done in FP64 is bound by the
+ * FP64 pipe, not by HBM.  QC_ARITH_F32X2 keeps the state in IEEE binary64 but
+ * computes each gate in float-float arithmetic on the FP32/integer pipes
+ * (operands split exactly into two floats, error-free products and sums),
+ * with a per-gate relative error of about 2^-46.  QC_ARITH_AUTO picks F32X2
+ * for complex128 and plain FP32 for complex64.
+ */
+typedef enum { QC_ARITH_AUTO = 0, QC_ARITH_NATIVE = 1, QC_ARITH_F32X2 = 2 } qc_arith;
+
+/* ---- state ---------------------------------------------------------------
+ * An opaque handle that owns (or borrows) 2^n amplitudes in device memory.
+ * Limits: 1 <= n <= 36 (the amplitude count is indexed with 64-bit ints).   */
+typedef struct qc_state qc_state;
+
+/* Allocate a library-owned state on the current device, initialised to
+ * |0...0>.  *out receives the handle.  QC_ERR_OOM if the device cannot hold
+ * 2^n * E bytes. */
+int qc_state_alloc(int n, int dtype, qc_state** out);
+
+/* Borrow caller-owned device memory (for instance a torch tensor) of 2^n
+ * amplitudes of `dtype`, 32-byte aligned (one 32-byte sector per access).  Its contents are used as the
+ * state; qc_state_free does not free it. */
+int qc_state_wrap(void* dev_ptr, int n, int dtype, qc_state** out);
+
+/* Release the handle (and the memory, when library-owned).  NULL is a no-op. */
+int qc_state_free(qc_state* s);
+
+/* Set the state to the computational basis state |x>, 0 <= x < 2^n. */
+int qc_state_set_basis(qc_state* s, uint64_t x);
+
+/* Copy all 2^n amplitudes device -> host (synchronous) or host -> device
+ * (ordered on the state's stream; the host buffer must stay valid until the
+ * stream reaches the copy when it is pinned, else the call is synchronous).
+ * `host` holds 2^n interleaved (re, im) pairs of the state's element type. */
+int qc_state_copy_to_host(const qc_state* s, void* host);
+int qc_state_copy_from_host(qc_state* s, const void* host);
+
+/* Query: device pointer, qubit count, dtype. */
+int qc_state_info(const qc_state* s, void** dev_ptr, int* n, int* dtype);
+
+/* Bind a cudaStream_t (passed as void*) on which all later work on `s` is
+ * enqueued.  NULL selects the legacy default stream. */
+int qc_set_stream(qc_state* s, void* cuda_stream);
+
+/* Select the arithmetic for complex128 gate sweeps (qc_arith). */
+int qc_set_arith(qc_state* s, int arith);
+
+/* ---- single gates --------------------------------------------------------
+ * qc_apply_1q: Sec. 2.1, Alg. 1.  U[8] = 2x2 complex row-major
+ * (u00, u01, u10, u11), each as (re, im).  For every pair of basis indices
+ * (a_j, b_j) that differ only in the target bit (0 in a_j, 1 in b_j):
+ *   psi[a_j] = u00 phi[a_j] + u01 phi[b_j];  psi[b_j] = u10 phi[a_j] + u11 phi[b_j].
+ * Diagonal, anti-diagonal and permutation matrices are detected and applied
+ * with the specialisations of Sec. 2.1 (Pauli X a swap, Z touching only b_j),
+ * which only move the amplitudes they change. */
+int qc_apply_1q(qc_state* s, const double U[8], int target);
+
+/* qc_apply_c1q: Sec. 2.2, Alg. 2, and Sec. 2.4 (multi-controlled gates).
+ * U acts on `target` only for basis indices whose bit of controls[i] equals
+ * control_states[i] (0 or 1) for every i < ncontrols; all other amplitudes
+ * are neither read nor written.  ncontrols may be 0.  Controls must be
+ * distinct and differ from the target. */
+int qc_apply_c1q(qc_state* s, const double U[8], const int* controls,
+                 const int* control_states, int ncontrols, int target);
+
+/* qc_apply_2q: Sec. 2.3, Alg. 3.  U4[32] = 4x4 complex row-major; the
+ * row/column index is 2*bit(q0) + bit(q1) (Eq. (1) order; the paper's Alg. 3
+ * labels the q0 offset as b_j, which contradicts Eq. (1) for non-symmetric
+ * U4 -- this library follows Eq. (1)).  q0 != q1, any order, any distance.
+ * SWAP is detected and only exchanges the two middle amplitudes. */
+int qc_apply_2q(qc_state* s, const double U4[32], int q0, int q1);
+
+/* qc_apply_kq: Sec. 2.4 (multi-qubit gates, generalised masks).  U is
+ * 2^k x 2^k complex (2 * 4^k doubles), 1 <= k <= 5, targets `qubits[0..k)`
+ * (qubits[0] = most significant index bit), optional controls as in
+ * qc_apply_c1q.  Used for fused gate blocks. */
+int qc_apply_kq(qc_state* s, const double* U, const int* qubits, int k,
+                const int* controls, const int* control_states, int ncontrols);
+
+/* ---- circuits ------------------------------------------------------------- */
+#define QC_MAX_TARGETS 5
+#define QC_MAX_CONTROLS 8
+
+/* Named gates of the paper's circuits (Fig. 1 QFT: H, CP, SWAP; Fig. 5
+ * Trotter circuit: Rz, Rx, CNOT) plus the usual Clifford+T set.
+ * P(theta) = diag(1, e^{i theta}); RX/RY/RZ(theta) = exp(-i theta P / 2). */
+typedef enum {
+  QC_GATE_MATRIX = 0, /* explicit matrix (2^nq x 2^nq) in `matrix` */
+  QC_GATE_H, QC_GATE_X, QC_GATE_Y, QC_GATE_Z, QC_GATE_S, QC_GATE_SDG,
+  QC_GATE_T, QC_GATE_TDG, QC_GATE_P, QC_GATE_RX, QC_GATE_RY, QC_GATE_RZ,
+  QC_GATE_SWAP
+} qc_gate_kind;
+
+typedef struct {
+  int kind;                         /* qc_gate_kind */
+  int nq;                           /* number of target qubits (1..5; SWAP: 2) */
+  int nc;                           /* number of controls (0..QC_MAX_CONTROLS) */
+  int qubits[QC_MAX_TARGETS];       /* targets, qubits[0] = MSB of U's index */
+  int controls[QC_MAX_CONTROLS];
+  int cstates[QC_MAX_CONTROLS];     /* 0 or 1 per control */
+  double theta;                     /* angle of P, RX, RY, RZ */
+  const double* matrix;             /* QC_GATE_MATRIX: 2 * 4^nq doubles, host memory */
+} qc_gate;
+
+typedef struct {
+  int fuse_k;      /* 0 or 1: apply gate by gate; 2..5: greedy fusion into
+                      k-qubit blocks applied as dense k-qubit gates */
+  int use_graph;   /* 1: capture the launches in a CUDA graph and replay it */
+  float* gate_ms;  /* optional host array of at least ngates entries: entry i
+                      receives the device time (ms) of launch i (a gate or a
+                      fused block; *nlaunch entries are written); synchronises.
+                      With use_graph the replay is timed as a whole and spread
+                      evenly over the launches. */
+  int* nlaunch;    /* optional out: number of kernel launches enqueued */
+} qc_opts;
+
+/* Apply `ngates` gates in order (Sec. 3: the circuit applies its gates one by
+ * one to the state).  opts may be NULL (defaults: no fusion, no graph). */
+int qc_apply_circuit(qc_state* s, const qc_gate* gates, int ngates, const qc_opts* opts);
+
+/* A k-qubit block produced by the fusion planner: dense U on `qubits`
+ * (qubits[0] = MSB of U's index), applied only where the controls hold. */
+typedef struct {
+  int k;
+  int qubits[QC_MAX_TARGETS];
+  int nc;
+  int controls[QC_MAX_CONTROLS];
+  int cstates[QC_MAX_CONTROLS];
+  double U[2 * 32 * 32];            /* 2^k x 2^k complex, row-major (re, im) */
+} qc_block;
+
+/* Host-only: the launch plan qc_apply_circuit would execute for these gates
+ * on an n-qubit state with fusion width fuse_k (0/1: none).  Writes at most
+ * max_blocks blocks and the total count to *nblocks (QC_ERR_ARG if more than
+ * max_blocks are needed).  Needs no GPU; used to inspect and test fusion. */
+int qc_fuse_plan(int n, const qc_gate* gates, int ngates, int fuse_k,
+                 qc_block* blocks, int max_blocks, int* nblocks);
+
+/* ---- observables ---------------------------------------------------------
+ * A Pauli sum H = sum_t coeffs[t] * P_t; term t consists of the (letter,
+ * qubit) pairs with indices offsets[t] .. offsets[t+1]-1 of `letters`
+ * ('X', 'Y', 'Z' or 'I') and `qubits`.  All arrays are host memory. */
+typedef struct {
+  int nterms;
+  const double* coeffs;  /* nterms */
+  const int* offsets;    /* nterms + 1 */
+  const char* letters;
+  const int* qubits;
+} qc_pauli_sum;
+
+/* *out = <psi| H |psi> (real part), reduced in FP64 on the device, then
+ * copied to the host (synchronises the state's stream).  The state is not
+ * modified. */
+int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+/* Message of the last failing call on this thread ("" if none). */
+const char* qc_last_error(void);
+/* Library version string. */
+const char* qc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QCGB300_H */

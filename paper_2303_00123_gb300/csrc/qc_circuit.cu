@@ -1,0 +1,354 @@
+// qc_circuit.cu -- circuit driver: named gates, greedy gate fusion, timing,
+// CUDA-graph capture.
+//
+// A circuit is applied gate by gate, each gate being one sweep over the
+// state (QCLAB++ Sec. 3 applies the circuit's gates in order; Sec. 4 notes
+// that the GPU time then scales with the number of gates).  With fuse_k >= 2
+// runs of gates are first merged on the host into dense k-qubit blocks, so
+// that one sweep applies many gates.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "qc_common.cuh"
+
+namespace {
+
+using cd = std::complex<double>;
+
+// Matrix of a named gate (host, FP64).  P(theta) = diag(1, e^{i theta});
+// RX/RY/RZ(theta) = exp(-i theta P / 2) (the rotation gates of Fig. 5).
+int named_matrix(const qc_gate& g, std::vector<cd>& U) {
+  const double r2 = 1.0 / std::sqrt(2.0);
+  const double t = g.theta;
+  const cd I(0, 1);
+  switch (g.kind) {
+    case QC_GATE_H: U = {r2, r2, r2, -r2}; return 1;
+    case QC_GATE_X: U = {0, 1, 1, 0}; return 1;
+    case QC_GATE_Y: U = {0, -I, I, 0}; return 1;
+    case QC_GATE_Z: U = {1, 0, 0, -1}; return 1;
+    case QC_GATE_S: U = {1, 0, 0, I}; return 1;
+    case QC_GATE_SDG: U = {1, 0, 0, -I}; return 1;
+    case QC_GATE_T: U = {1, 0, 0, std::polar(1.0, M_PI / 4)}; return 1;
+    case QC_GATE_TDG: U = {1, 0, 0, std::polar(1.0, -M_PI / 4)}; return 1;
+    case QC_GATE_P: U = {1, 0, 0, std::polar(1.0, t)}; return 1;
+    case QC_GATE_RX: U = {std::cos(t / 2), -I * std::sin(t / 2), -I * std::sin(t / 2), std::cos(t / 2)}; return 1;
+    case QC_GATE_RY: U = {std::cos(t / 2), -std::sin(t / 2), std::sin(t / 2), std::cos(t / 2)}; return 1;
+    case QC_GATE_RZ: U = {std::polar(1.0, -t / 2), 0, 0, std::polar(1.0, t / 2)}; return 1;
+    case QC_GATE_SWAP: U.assign(16, 0); U[0] = U[6] = U[9] = U[15] = 1; return 2;
+    default: return 0;
+  }
+}
+
+// Resolve a gate record into (targets, controls, matrix) and validate it.
+struct Resolved {
+  int k, nc;
+  int t[QC_MAX_TARGETS], c[QC_MAX_CONTROLS], cs[QC_MAX_CONTROLS];
+  std::vector<cd> U;
+};
+
+int resolve(int n, const qc_gate& g, Resolved& R) {
+  int k;
+  if (g.kind == QC_GATE_MATRIX) {
+    k = g.nq;
+    if (k < 1 || k > QC_MAX_TARGETS) return qc_fail(QC_ERR_ARG, "matrix gate with nq=%d", g.nq);
+    if (!g.matrix) return qc_fail(QC_ERR_ARG, "matrix gate without a matrix");
+    const int D = 1 << k;
+    R.U.resize((size_t)D * D);
+    for (int i = 0; i < D * D; i++) R.U[i] = cd(g.matrix[2 * i], g.matrix[2 * i + 1]);
+  } else {
+    k = named_matrix(g, R.U);
+    if (k == 0) return qc_fail(QC_ERR_ARG, "unknown gate kind %d", g.kind);
+    if (g.nq != k) return qc_fail(QC_ERR_ARG, "gate kind %d acts on %d qubit(s), nq=%d", g.kind, k, g.nq);
+  }
+  if (g.nc < 0 || g.nc > QC_MAX_CONTROLS) return qc_fail(QC_ERR_ARG, "gate with nc=%d", g.nc);
+  if (int rc = qc_check_qubits(n, g.qubits, k, g.controls, g.cstates, g.nc)) return rc;
+  R.k = k;
+  R.nc = g.nc;
+  for (int i = 0; i < k; i++) R.t[i] = g.qubits[i];
+  for (int i = 0; i < g.nc; i++) { R.c[i] = g.controls[i]; R.cs[i] = g.cstates[i]; }
+  return QC_OK;
+}
+
+void to_op(int n, const Resolved& R, qc_op& op) {
+  op.k = R.k;
+  op.nc = R.nc;
+  for (int i = 0; i < R.k; i++) op.tpos[i] = n - 1 - R.t[i];
+  for (int i = 0; i < R.nc; i++) { op.cpos[i] = n - 1 - R.c[i]; op.cval[i] = R.cs[i]; }
+  const size_t D = (size_t)1 << R.k;
+  for (size_t i = 0; i < D * D; i++) { op.U[2 * i] = R.U[i].real(); op.U[2 * i + 1] = R.U[i].imag(); }
+}
+
+// ---------------------------------------------------------------- fusion
+// A fused block: qubits q[0..m) (q[0] = most significant bit of the block
+// index) and its 2^m x 2^m unitary, accumulated in FP64.  A block's columns
+// are states of an m-qubit register, so appending a gate applies that gate
+// to every column.
+struct Block {
+  std::vector<int> q;
+  std::vector<cd> M;     // row-major
+  int ngates = 0;
+  int first = -1;        // index of the first gate (single-gate blocks keep it)
+};
+
+int local_index(const Block& b, int qubit) {
+  for (size_t i = 0; i < b.q.size(); i++) if (b.q[i] == qubit) return (int)i;
+  return -1;
+}
+
+// Tensor product: b <- b (x) o (b's qubits stay the most significant).
+void kron_into(Block& b, const Block& o) {
+  const int ma = (int)b.q.size(), mb = (int)o.q.size();
+  const int da = 1 << ma, db = 1 << mb, d = da * db;
+  std::vector<cd> M((size_t)d * d);
+  for (int ra = 0; ra < da; ra++)
+    for (int ca = 0; ca < da; ca++) {
+      const cd x = b.M[(size_t)ra * da + ca];
+      if (x == cd(0)) continue;
+      for (int rb = 0; rb < db; rb++)
+        for (int cb = 0; cb < db; cb++)
+          M[(size_t)(ra * db + rb) * d + (ca * db + cb)] = x * o.M[(size_t)rb * db + cb];
+    }
+  b.q.insert(b.q.end(), o.q.begin(), o.q.end());
+  b.M.swap(M);
+  b.ngates += o.ngates;
+  if (o.first >= 0 && (b.first < 0 || o.first < b.first)) b.first = o.first;
+}
+
+Block single_qubit_identity(int qubit) {
+  Block b;
+  b.q = {qubit};
+  b.M = {1, 0, 0, 1};
+  return b;
+}
+
+// Apply a resolved gate to the block's matrix (left-multiply).
+void block_apply(Block& b, const Resolved& R) {
+  const int m = (int)b.q.size();
+  const int d = 1 << m;
+  int tl[QC_MAX_TARGETS], cl[QC_MAX_CONTROLS];
+  for (int i = 0; i < R.k; i++) tl[i] = m - 1 - local_index(b, R.t[i]);   // bit positions in block index
+  for (int i = 0; i < R.nc; i++) cl[i] = m - 1 - local_index(b, R.c[i]);
+  const int kd = 1 << R.k;
+  std::vector<cd> in(kd);
+  for (int col = 0; col < d; col++) {
+    for (int x = 0; x < d; x++) {
+      bool first = true;
+      for (int i = 0; i < R.k; i++) if ((x >> tl[i]) & 1) first = false;
+      if (!first) continue;
+      bool ok = true;
+      for (int i = 0; i < R.nc; i++) if (((x >> cl[i]) & 1) != R.cs[i]) ok = false;
+      if (!ok) continue;
+      int idx[1 << QC_MAX_TARGETS];
+      for (int r = 0; r < kd; r++) {
+        int y = x;
+        for (int i = 0; i < R.k; i++) if ((r >> (R.k - 1 - i)) & 1) y |= 1 << tl[i];
+        idx[r] = y;
+        in[r] = b.M[(size_t)y * d + col];
+      }
+      for (int r = 0; r < kd; r++) {
+        cd acc = 0;
+        for (int c = 0; c < kd; c++) acc += R.U[(size_t)r * kd + c] * in[c];
+        b.M[(size_t)idx[r] * d + col] = acc;
+      }
+    }
+  }
+  b.ngates++;
+}
+
+struct Emitted {
+  bool single;      // apply the original gate
+  int gate;         // its index
+  Block block;
+};
+
+// Greedy fusion with several open blocks on disjoint qubit sets: a gate joins
+// (and merges) the open blocks it touches when the union has at most kmax
+// qubits; otherwise those blocks are emitted and the gate opens a new block.
+// Blocks on disjoint qubits commute, so emission order stays valid.
+void fuse(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Emitted>& out) {
+  std::vector<Block> open;
+  std::vector<int> owner(n, -1);   // qubit -> open block index
+  auto emit = [&](int bi) {
+    Block& b = open[bi];
+    Emitted e;
+    e.single = (b.ngates == 1);
+    e.gate = b.first;
+    if (!e.single) e.block = b;
+    out.push_back(std::move(e));
+    for (int q : b.q) owner[q] = -1;
+    b.q.clear();
+    b.ngates = 0;
+  };
+  for (int gi = 0; gi < (int)gates.size(); gi++) {
+    const Resolved& R = gates[gi];
+    std::vector<int> qs(R.t, R.t + R.k);
+    qs.insert(qs.end(), R.c, R.c + R.nc);
+    std::vector<int> touched;
+    int width = 0;
+    for (int q : qs) {
+      const int o = owner[q];
+      if (o < 0) width++;
+      else if (std::find(touched.begin(), touched.end(), o) == touched.end()) touched.push_back(o);
+    }
+    for (int o : touched) width += (int)open[o].q.size();
+    if ((int)qs.size() > kmax) {          // wider than a block: applied on its own
+      for (int o : touched) emit(o);
+      Emitted e;
+      e.single = true;
+      e.gate = gi;
+      out.push_back(std::move(e));
+      continue;
+    }
+    if (width > kmax) {
+      for (int o : touched) emit(o);
+      touched.clear();
+    }
+    // merge the touched blocks (if any) into one
+    Block nb;
+    if (touched.empty()) {
+      nb.ngates = 0;
+    } else {
+      std::sort(touched.begin(), touched.end());
+      nb = open[touched[0]];
+      for (size_t i = 1; i < touched.size(); i++) kron_into(nb, open[touched[i]]);
+      for (int o : touched) { for (int q : open[o].q) owner[q] = -1; open[o].q.clear(); open[o].ngates = 0; }
+    }
+    for (int q : qs)
+      if (local_index(nb, q) < 0) {
+        Block id = single_qubit_identity(q);
+        if (nb.q.empty()) { nb.q = id.q; nb.M = id.M; }
+        else kron_into(nb, id);
+      }
+    block_apply(nb, R);
+    if (nb.first < 0) nb.first = gi;
+    int slot = -1;
+    for (int i = 0; i < (int)open.size(); i++) if (open[i].q.empty()) { slot = i; break; }
+    if (slot < 0) { slot = (int)open.size(); open.emplace_back(); }
+    open[slot] = std::move(nb);
+    for (int q : open[slot].q) owner[q] = slot;
+  }
+  // flush in order of first gate
+  std::vector<int> rest;
+  for (int i = 0; i < (int)open.size(); i++) if (!open[i].q.empty()) rest.push_back(i);
+  std::sort(rest.begin(), rest.end(), [&](int a, int b) { return open[a].first < open[b].first; });
+  for (int i : rest) emit(i);
+}
+
+}  // namespace
+
+namespace {
+// Build the launch plan (shared by qc_apply_circuit and qc_fuse_plan).
+int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops) {
+  if (ngates < 0 || (ngates > 0 && !gates)) return qc_fail(QC_ERR_ARG, "invalid gate list");
+  if (fuse_k < 0 || fuse_k > QC_MAX_TARGETS) return qc_fail(QC_ERR_ARG, "fuse_k=%d out of range 0..5", fuse_k);
+  std::vector<Resolved> res(ngates);
+  for (int i = 0; i < ngates; i++)
+    if (int rc = resolve(n, gates[i], res[i])) return qc_fail(rc, "gate %d: %s", i, qc_last_error());
+  ops.clear();
+  if (fuse_k >= 2) {
+    std::vector<Emitted> em;
+    fuse(n, res, std::min(fuse_k, n), em);
+    ops.resize(em.size());
+    for (size_t i = 0; i < em.size(); i++) {
+      if (em[i].single) { to_op(n, res[em[i].gate], ops[i]); continue; }
+      const Block& b = em[i].block;
+      Resolved R;
+      R.k = (int)b.q.size();
+      R.nc = 0;
+      for (int j = 0; j < R.k; j++) R.t[j] = b.q[j];
+      R.U = b.M;
+      to_op(n, R, ops[i]);
+    }
+  } else {
+    ops.resize(ngates);
+    for (int i = 0; i < ngates; i++) to_op(n, res[i], ops[i]);
+  }
+  return QC_OK;
+}
+}  // namespace
+
+extern "C" int qc_fuse_plan(int n, const qc_gate* gates, int ngates, int fuse_k, qc_block* blocks,
+                            int max_blocks, int* nblocks) {
+  if (n < 1 || n > 36) return qc_fail(QC_ERR_ARG, "n=%d out of range 1..36", n);
+  if (!nblocks) return qc_fail(QC_ERR_ARG, "nblocks is NULL");
+  std::vector<qc_op> ops;
+  if (int rc = plan_ops(n, gates, ngates, fuse_k, ops)) return rc;
+  *nblocks = (int)ops.size();
+  if ((int)ops.size() > max_blocks || (!blocks && !ops.empty()))
+    return qc_fail(QC_ERR_ARG, "plan needs %d blocks, buffer holds %d", (int)ops.size(), max_blocks);
+  for (size_t i = 0; i < ops.size(); i++) {
+    const qc_op& op = ops[i];
+    qc_block& b = blocks[i];
+    std::memset(&b, 0, sizeof(b));
+    b.k = op.k;
+    for (int j = 0; j < op.k; j++) b.qubits[j] = n - 1 - op.tpos[j];
+    b.nc = op.nc;
+    for (int j = 0; j < op.nc; j++) { b.controls[j] = n - 1 - op.cpos[j]; b.cstates[j] = op.cval[j]; }
+    const size_t D = (size_t)1 << op.k;
+    std::memcpy(b.U, op.U, sizeof(double) * 2 * D * D);
+  }
+  return QC_OK;
+}
+
+extern "C" int qc_apply_circuit(qc_state* s, const qc_gate* gates, int ngates, const qc_opts* opts) {
+  if (int rc = qc_check_state(s)) return rc;
+  qc_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.use_graph && s->stream == nullptr) return qc_fail(QC_ERR_ARG, "graph capture needs a non-default stream (qc_set_stream)");
+
+  std::vector<qc_op> ops;
+  if (int rc = plan_ops(s->n, gates, ngates, o.fuse_k, ops)) return rc;
+  if (o.nlaunch) *o.nlaunch = (int)ops.size();
+
+  std::vector<cudaEvent_t> ev;
+  if (o.gate_ms) {
+    ev.resize(ops.size() + 1);
+    for (auto& e : ev) QC_CUDA(cudaEventCreate(&e));
+  }
+  cudaGraph_t graph = nullptr;
+  if (o.use_graph) QC_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = QC_OK;
+  if (o.gate_ms && !o.use_graph) cudaEventRecord(ev[0], s->stream);
+  for (size_t i = 0; i < ops.size() && rc == QC_OK; i++) {
+    rc = qc_launch_op(s, ops[i]);
+    if (o.gate_ms && !o.use_graph) cudaEventRecord(ev[i + 1], s->stream);
+  }
+  if (o.use_graph) {
+    cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+    if (rc == QC_OK && e != cudaSuccess) rc = qc_cuda_fail(e, "cudaStreamEndCapture");
+    if (rc == QC_OK) {
+      cudaGraphExec_t exec = nullptr;
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      if (e != cudaSuccess) rc = qc_cuda_fail(e, "cudaGraphInstantiate");
+      else {
+        if (o.gate_ms) cudaEventRecord(ev[0], s->stream);
+        e = cudaGraphLaunch(exec, s->stream);
+        if (e != cudaSuccess) rc = qc_cuda_fail(e, "cudaGraphLaunch");
+        if (o.gate_ms) cudaEventRecord(ev[ops.size()], s->stream);
+        cudaGraphExecDestroy(exec);
+      }
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  if (o.gate_ms && rc == QC_OK) {
+    cudaError_t e = cudaEventSynchronize(ev.back());
+    if (e != cudaSuccess) rc = qc_cuda_fail(e, "cudaEventSynchronize");
+    for (size_t i = 0; i < ops.size() && rc == QC_OK; i++) {
+      float ms = 0.f;
+      if (o.use_graph) {   // only the whole replay is timed; spread evenly
+        if (i == 0) cudaEventElapsedTime(&ms, ev[0], ev[ops.size()]);
+        o.gate_ms[i] = 0.f;
+        if (i == 0) for (size_t j = 0; j < ops.size(); j++) o.gate_ms[j] = ms / ops.size();
+      } else {
+        cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+        o.gate_ms[i] = ms;
+      }
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return rc;
+}

@@ -1,0 +1,274 @@
+// qc_common.cuh -- shared definitions of the GB300 gate engine (device + host).
+//
+// Index convention (QCLAB++ Definition 1): qubit q of an n-qubit register is
+// bit position p = n-1-q of the basis index, i.e. it has stride 2^p.  All
+// kernels work with bit positions; the host converts qubit numbers once.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qcgb300.h"
+
+// --------------------------------------------------------------------------
+// Library state handle
+// --------------------------------------------------------------------------
+struct qc_state {
+  void* ptr;            // 2^n amplitudes, interleaved (re, im)
+  int n;                // qubits
+  int dtype;            // QC_C64 / QC_C128
+  int owned;            // 1: allocated by qc_state_alloc
+  int arith;            // qc_arith for QC_C128
+  int device;           // CUDA device ordinal the memory lives on
+  cudaStream_t stream;  // work queue
+};
+
+// --------------------------------------------------------------------------
+// Errors (thread-local message, negative status codes)
+// --------------------------------------------------------------------------
+int qc_fail(int code, const char* fmt, ...);
+int qc_cuda_fail(cudaError_t e, const char* what);
+#define QC_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t qc_e_ = (call);                        \
+    if (qc_e_ != cudaSuccess) return qc_cuda_fail(qc_e_, #call); \
+  } while (0)
+#define QC_LAUNCHED(what)                              \
+  do {                                                 \
+    cudaError_t qc_e_ = cudaGetLastError();            \
+    if (qc_e_ != cudaSuccess) return qc_cuda_fail(qc_e_, what); \
+  } while (0)
+
+// Validate a handle; sets the CUDA device of the state current.
+int qc_check_state(const qc_state* s);
+
+// Validate target/control qubit numbers (range, distinctness, states 0/1).
+int qc_check_qubits(int n, const int* t, int k, const int* c, const int* cs, int nc);
+
+// Number of SMs of the current device (cached).
+int qc_num_sms();
+
+// --------------------------------------------------------------------------
+// Index arithmetic
+// --------------------------------------------------------------------------
+// Insert a zero bit at position p of x (bits >= p move up by one).  Applying
+// this for the sorted positions of the gate's targets and controls maps a
+// loop counter j onto the first index of its group -- the paper's masks
+// m_L, m_C, m_R of Alg. 1-3 (Eqs. (9)-(10), (16)-(19)), generalised to any
+// number of positions as Sec. 2.4 describes.
+__host__ __device__ __forceinline__ uint64_t qc_insert_zero(uint64_t x, int p) {
+  const uint64_t lo = x & ((1ull << p) - 1ull);
+  return ((x ^ lo) << 1) | lo;
+}
+
+#define QC_MAX_INS (QC_MAX_TARGETS + QC_MAX_CONTROLS)
+
+// --------------------------------------------------------------------------
+// 32-byte vector memory access (one DRAM sector per thread access)
+// --------------------------------------------------------------------------
+struct __align__(32) vec32 { uint32_t w[8]; };
+
+__device__ __forceinline__ vec32 qc_ld32(const void* p) {
+  vec32 v;
+  asm volatile("ld.global.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v.w[0]), "=r"(v.w[1]), "=r"(v.w[2]), "=r"(v.w[3]),
+                 "=r"(v.w[4]), "=r"(v.w[5]), "=r"(v.w[6]), "=r"(v.w[7])
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void qc_st32(void* p, const vec32& v) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+               :: "l"(p), "r"(v.w[0]), "r"(v.w[1]), "r"(v.w[2]), "r"(v.w[3]),
+                  "r"(v.w[4]), "r"(v.w[5]), "r"(v.w[6]), "r"(v.w[7])
+               : "memory");
+}
+
+// --------------------------------------------------------------------------
+// Arithmetic policies.  Each provides
+//   V, E       -- amplitudes per 32-byte vector, bytes per amplitude
+//   val_t      -- in-register amplitude
+//   coef_t     -- in-kernel form of one complex matrix entry (make_coef on host)
+//   load(v, e) / store(v, e, x) -- amplitude e of a 32-byte vector
+//   dot<K>(row, x) = sum_k row[k] * x[k]
+// Amplitudes a kernel does not change are never passed through load/store,
+// so they stay bit-exact.
+// --------------------------------------------------------------------------
+
+// complex64 state, FP32 arithmetic.
+struct ArC64 {
+  static constexpr int V = 4;
+  static constexpr int E = 8;
+  struct val_t { float re, im; };
+  struct coef_t { float re, im; };
+  static __host__ coef_t make_coef(double re, double im) { return {(float)re, (float)im}; }
+  static __device__ __forceinline__ val_t load(const vec32& v, int e) {
+    return {__uint_as_float(v.w[2 * e]), __uint_as_float(v.w[2 * e + 1])};
+  }
+  static __device__ __forceinline__ void store(vec32& v, int e, const val_t& x) {
+    v.w[2 * e] = __float_as_uint(x.re); v.w[2 * e + 1] = __float_as_uint(x.im);
+  }
+  template <int K>
+  static __device__ __forceinline__ val_t dot(const coef_t* c, const val_t* x) {
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      re = fmaf(c[k].re, x[k].re, re); re = fmaf(-c[k].im, x[k].im, re);
+      im = fmaf(c[k].re, x[k].im, im); im = fmaf(c[k].im, x[k].re, im);
+    }
+    return {re, im};
+  }
+};
+
+// complex128 state, native FP64 arithmetic (bound by GB300's FP64 rate).
+struct ArC128 {
+  static constexpr int V = 2;
+  static constexpr int E = 16;
+  struct val_t { double re, im; };
+  struct coef_t { double re, im; };
+  static __host__ coef_t make_coef(double re, double im) { return {re, im}; }
+  static __device__ __forceinline__ val_t load(const vec32& v, int e) {
+    return {__hiloint2double((int)v.w[4 * e + 1], (int)v.w[4 * e]),
+            __hiloint2double((int)v.w[4 * e + 3], (int)v.w[4 * e + 2])};
+  }
+  static __device__ __forceinline__ void store(vec32& v, int e, const val_t& x) {
+    v.w[4 * e] = (uint32_t)__double2loint(x.re); v.w[4 * e + 1] = (uint32_t)__double2hiint(x.re);
+    v.w[4 * e + 2] = (uint32_t)__double2loint(x.im); v.w[4 * e + 3] = (uint32_t)__double2hiint(x.im);
+  }
+  template <int K>
+  static __device__ __forceinline__ val_t dot(const coef_t* c, const val_t* x) {
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      re = fma(c[k].re, x[k].re, re); re = fma(-c[k].im, x[k].im, re);
+      im = fma(c[k].re, x[k].im, im); im = fma(c[k].im, x[k].re, im);
+    }
+    return {re, im};
+  }
+};
+
+// complex128 state (IEEE binary64 in memory), float-float arithmetic on the
+// FP32 and integer pipes.
+//
+// Why: GB300 executes FP64 FMA and f64<->f32 conversions at about 2 per clock
+// per SM against 128 FP32 FMA, so a dense complex128 sweep done in FP64
+// cannot keep up with HBM.  Here each input double is split exactly into two
+// floats with integer bit operations (the double-single representation of
+// Dekker 1971), products are formed error-free with an FMA (TwoProduct) and
+// running sums with Knuth's TwoSum, and each real output is rebuilt from its
+// two float parts (converted to doubles by integer bit operations) with a
+// single FP64 add -- the only FP64-pipe instruction per output.
+//
+// Accuracy: the split keeps the leading 47 significand bits of each input
+// (relative error < 2^-46); each real output carries an error of about
+// 2^-46 * sum_k |u_k| |x_k|.  Range: inputs with |x| < 2^-100 are flushed to
+// zero (absolute error < 1e-30); |x| must stay below 2^127.
+struct ArC128x {
+  static constexpr int V = 2;
+  static constexpr int E = 16;
+  struct ff { float h, l; };
+  struct val_t { ff re, im; };
+  // One complex entry u = ur + i ui, split as ur = rh + rl, ui = ih + il.
+  struct coef_t { float rh, rl, ih, il; };
+  static __host__ coef_t make_coef(double re, double im) {
+    coef_t c;
+    c.rh = (float)re; c.rl = (float)(re - (double)c.rh);
+    c.ih = (float)im; c.il = (float)(im - (double)c.ih);
+    return c;
+  }
+  // IEEE double given as (low word, high word) -> (hi, lo) floats.
+  static __device__ __forceinline__ ff split(uint32_t w0, uint32_t w1) {
+    // hi: keep the sign, rebias the exponent (1023 -> 127) and keep the
+    // leading 23 explicit mantissa bits (20 from w1, 3 from w0): truncation.
+    const uint32_t t = w1 - 0x38000000u;
+    uint32_t h = __funnelshift_l(w0, t, 3);
+    h = (h & 0x7FFFFFFFu) | (w1 & 0x80000000u);
+    // lo: the next 23 mantissa bits m (w0 bits 28..6) weigh 2^(E-46); the
+    // float difference (1.m * 2^(E-23)) - 2^(E-23) is exact and equals that.
+    const uint32_t base = (h & 0xFF800000u) - 0x0B800000u;
+    const uint32_t f1 = ((w0 >> 6) & 0x007FFFFFu) | base;
+    const float lo = __uint_as_float(f1) - __uint_as_float(base);
+    const bool tiny = (w1 & 0x7FFFFFFFu) < 0x39B00000u;  // |x| < 2^-100, or 0
+    ff r;
+    r.h = tiny ? 0.f : __uint_as_float(h);
+    r.l = tiny ? 0.f : lo;
+    return r;
+  }
+  // float -> IEEE double bits, exact for normal floats (zero/subnormal -> +-0).
+  static __device__ __forceinline__ double f2d(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t m = b & 0x7FFFFFFFu;
+    const bool z = m < 0x00800000u;
+    const uint32_t hi = z ? (b & 0x80000000u) : (((m >> 3) + 0x38000000u) | (b & 0x80000000u));
+    const uint32_t lo = z ? 0u : (b << 29);
+    return __hiloint2double((int)hi, (int)lo);
+  }
+  static __device__ __forceinline__ val_t load(const vec32& v, int e) {
+    return {split(v.w[4 * e], v.w[4 * e + 1]), split(v.w[4 * e + 2], v.w[4 * e + 3])};
+  }
+  // x holds unnormalised (s, c) pairs; the double is s + c rounded once.
+  static __device__ __forceinline__ void store(vec32& v, int e, const val_t& x) {
+    const double re = f2d(x.re.h) + f2d(x.re.l);
+    const double im = f2d(x.im.h) + f2d(x.im.l);
+    v.w[4 * e] = (uint32_t)__double2loint(re); v.w[4 * e + 1] = (uint32_t)__double2hiint(re);
+    v.w[4 * e + 2] = (uint32_t)__double2loint(im); v.w[4 * e + 3] = (uint32_t)__double2hiint(im);
+  }
+  // Running float-float accumulator: s is the rounded sum of the leading
+  // products, c collects their exact rounding errors and the cross terms.
+  struct acc_t { float s, c; };
+  static __device__ __forceinline__ void acc_first(acc_t& a, float uh, float ul, const ff& x) {
+    const float p = uh * x.h;
+    a.s = p;
+    a.c = fmaf(uh, x.h, -p);          // exact error of the product
+    a.c = fmaf(uh, x.l, a.c);
+    a.c = fmaf(ul, x.h, a.c);
+  }
+  static __device__ __forceinline__ void acc_add(acc_t& a, float uh, float ul, const ff& x) {
+    const float p = uh * x.h;
+    const float e = fmaf(uh, x.h, -p);
+    const float t = a.s + p;          // TwoSum(s, p)
+    const float z = t - a.s;
+    const float err = (a.s - (t - z)) + (p - z);
+    a.s = t;
+    a.c += err + e;
+    a.c = fmaf(uh, x.l, a.c);
+    a.c = fmaf(ul, x.h, a.c);
+  }
+  template <int K>
+  static __device__ __forceinline__ val_t dot(const coef_t* c, const val_t* x) {
+    // re = sum ur*xr - ui*xi ;  im = sum ur*xi + ui*xr
+    acc_t re, im;
+    acc_first(re, c[0].rh, c[0].rl, x[0].re);
+    acc_add(re, -c[0].ih, -c[0].il, x[0].im);
+    acc_first(im, c[0].rh, c[0].rl, x[0].im);
+    acc_add(im, c[0].ih, c[0].il, x[0].re);
+#pragma unroll
+    for (int k = 1; k < K; k++) {
+      acc_add(re, c[k].rh, c[k].rl, x[k].re);
+      acc_add(re, -c[k].ih, -c[k].il, x[k].im);
+      acc_add(im, c[k].rh, c[k].rl, x[k].im);
+      acc_add(im, c[k].ih, c[k].il, x[k].re);
+    }
+    val_t r;
+    r.re.h = re.s; r.re.l = re.c;
+    r.im.h = im.s; r.im.l = im.c;
+    return r;
+  }
+};
+
+// --------------------------------------------------------------------------
+// Host-side gate description handed to the launchers
+// --------------------------------------------------------------------------
+enum qc_struct { QC_ST_DENSE = 0, QC_ST_PERM = 1, QC_ST_PHASE = 2 };
+
+struct qc_op {
+  int k;                        // number of targets
+  int tpos[QC_MAX_TARGETS];     // target bit positions, tpos[0] = MSB of U's index
+  int nc;                       // controls
+  int cpos[QC_MAX_CONTROLS];    // control bit positions
+  int cval[QC_MAX_CONTROLS];    // control states
+  double U[2 * 32 * 32];        // 2^k x 2^k complex, row-major (re, im)
+};
+
+// Apply one (controlled) k-qubit gate given by its matrix; the launcher
+// classifies the matrix (dense / permutation / diagonal) and picks a kernel.
+int qc_launch_op(qc_state* s, const qc_op& op);

@@ -1,0 +1,300 @@
+"""Thin ctypes binding of the C ABI declared in ``include/qcgb300.h``.
+
+Only argument marshalling lives here; every step of a gate sweep runs in the
+CUDA kernels of ``libqcgb300.so``.  PyTorch is used for device memory and
+streams (``State.from_tensor`` borrows a tensor's storage).  There is no CPU
+fallback: importing this module fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqcgb300.so")
+
+QC_OK, QC_ERR_ARG, QC_ERR_OOM, QC_ERR_CUDA, QC_ERR_TIMEOUT, QC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+C64, C128 = 0, 1
+ARITH_AUTO, ARITH_NATIVE, ARITH_F32X2 = 0, 1, 2
+MAX_TARGETS, MAX_CONTROLS = 5, 8
+
+GATE_KIND = {"MATRIX": 0, "U": 0, "U4": 0, "UK": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "SDG": 6,
+             "T": 7, "TDG": 8, "P": 9, "RX": 10, "RY": 11, "RZ": 12, "SWAP": 13}
+
+
+class QCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("qcgb300 error %d: %s" % (code, msg))
+        self.code = code
+
+
+class qc_gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nq", ctypes.c_int), ("nc", ctypes.c_int),
+                ("qubits", ctypes.c_int * MAX_TARGETS), ("controls", ctypes.c_int * MAX_CONTROLS),
+                ("cstates", ctypes.c_int * MAX_CONTROLS), ("theta", ctypes.c_double),
+                ("matrix", ctypes.POINTER(ctypes.c_double))]
+
+
+class qc_opts(ctypes.Structure):
+    _fields_ = [("fuse_k", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("gate_ms", ctypes.POINTER(ctypes.c_float)), ("nlaunch", ctypes.POINTER(ctypes.c_int))]
+
+
+class qc_block(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("qubits", ctypes.c_int * MAX_TARGETS), ("nc", ctypes.c_int),
+                ("controls", ctypes.c_int * MAX_CONTROLS), ("cstates", ctypes.c_int * MAX_CONTROLS),
+                ("U", ctypes.c_double * (2 * 32 * 32))]
+
+
+class qc_pauli_sum(ctypes.Structure):
+    _fields_ = [("nterms", ctypes.c_int), ("coeffs", ctypes.POINTER(ctypes.c_double)),
+                ("offsets", ctypes.POINTER(ctypes.c_int)), ("letters", ctypes.c_char_p),
+                ("qubits", ctypes.POINTER(ctypes.c_int))]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libqcgb300.so not found at %s: run `python -c 'import __graft_entry__ as g; "
+                          "g.build()'` (needs nvcc for sm_103a)" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    IP = ctypes.POINTER(ctypes.c_int)
+    DP = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "qc_state_alloc": [I, I, ctypes.POINTER(P)],
+        "qc_state_wrap": [P, I, I, ctypes.POINTER(P)],
+        "qc_state_free": [P],
+        "qc_state_set_basis": [P, ctypes.c_uint64],
+        "qc_state_copy_to_host": [P, P],
+        "qc_state_copy_from_host": [P, P],
+        "qc_state_info": [P, ctypes.POINTER(P), IP, IP],
+        "qc_set_stream": [P, P],
+        "qc_set_arith": [P, I],
+        "qc_apply_1q": [P, DP, I],
+        "qc_apply_c1q": [P, DP, IP, IP, I, I],
+        "qc_apply_2q": [P, DP, I, I],
+        "qc_apply_kq": [P, DP, IP, I, IP, IP, I],
+        "qc_apply_circuit": [P, ctypes.POINTER(qc_gate), I, ctypes.POINTER(qc_opts)],
+        "qc_expect": [P, ctypes.POINTER(qc_pauli_sum), DP],
+        "qc_fuse_plan": [I, ctypes.POINTER(qc_gate), I, I, ctypes.POINTER(qc_block), I, IP],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.qc_last_error.restype = ctypes.c_char_p
+    lib.qc_last_error.argtypes = []
+    lib.qc_version.restype = ctypes.c_char_p
+    lib.qc_version.argtypes = []
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc):
+    if rc != QC_OK:
+        raise QCError(rc, lib.qc_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iarr(seq):
+    seq = [int(v) for v in seq]
+    return (ctypes.c_int * max(1, len(seq)))(*seq)
+
+
+def _mat(U) -> np.ndarray:
+    """Complex matrix -> contiguous float64 (re, im) pairs."""
+    U = np.ascontiguousarray(np.asarray(U, dtype=np.complex128))
+    return U.view(np.float64).reshape(-1).copy()
+
+
+# ------------------------------------------------------------------ records
+def gate_records(gates):
+    """Convert gate objects (name, qubits, controls, cstates, theta, matrix)
+    into a ctypes array of qc_gate; returns (array, keepalive)."""
+    arr = (qc_gate * max(1, len(gates)))()
+    keep = []
+    for i, g in enumerate(gates):
+        name = g.name.upper()
+        if name not in GATE_KIND:
+            raise QCError(QC_ERR_ARG, "unknown gate name %r" % g.name)
+        r = arr[i]
+        r.kind = GATE_KIND[name]
+        r.nq = len(g.qubits)
+        controls = tuple(getattr(g, "controls", ()) or ())
+        cstates = tuple(getattr(g, "cstates", ()) or ()) or (1,) * len(controls)
+        if r.nq > MAX_TARGETS or len(controls) > MAX_CONTROLS:
+            raise QCError(QC_ERR_ARG, "gate %d too wide" % i)
+        r.nc = len(controls)
+        for j, q in enumerate(g.qubits):
+            r.qubits[j] = int(q)
+        for j, (c, s) in enumerate(zip(controls, cstates)):
+            r.controls[j] = int(c)
+            r.cstates[j] = int(s)
+        r.theta = float(g.theta) if getattr(g, "theta", None) is not None else 0.0
+        if r.kind == 0:
+            m = _mat(g.matrix)
+            keep.append(m)
+            r.matrix = _dptr(m)
+    return arr, keep
+
+
+def pauli_record(hamiltonian):
+    """[(coeff, [(letter, qubit), ...]), ...] -> (qc_pauli_sum, keepalive)."""
+    coeffs = np.array([float(c) for c, _ in hamiltonian], dtype=np.float64)
+    offsets, letters, qubits = [0], [], []
+    for _, ops in hamiltonian:
+        for letter, q in ops:
+            letters.append(letter.upper())
+            qubits.append(int(q))
+        offsets.append(len(letters))
+    offs = _iarr(offsets)
+    qs = _iarr(qubits)
+    lt = ctypes.create_string_buffer("".join(letters).encode(), max(1, len(letters)))
+    rec = qc_pauli_sum(len(coeffs), _dptr(coeffs) if len(coeffs) else None, offs,
+                       ctypes.cast(lt, ctypes.c_char_p), qs)
+    return rec, (coeffs, offs, qs, lt)
+
+
+# ------------------------------------------------------------------ state
+class State:
+    """A 2^n-amplitude state in device memory (library-owned or borrowed)."""
+
+    def __init__(self, n: int, dtype: int = C128, handle=None, tensor=None):
+        self.n = n
+        self.dtype = dtype
+        self._tensor = tensor
+        if handle is None:
+            h = ctypes.c_void_p()
+            _check(lib.qc_state_alloc(n, dtype, ctypes.byref(h)))
+            handle = h
+        self._h = handle
+
+    @classmethod
+    def from_tensor(cls, t):
+        """Borrow a contiguous torch.complex64/complex128 CUDA tensor of 2^n entries."""
+        import torch
+        if not t.is_cuda or not t.is_contiguous():
+            raise QCError(QC_ERR_ARG, "tensor must be a contiguous CUDA tensor")
+        dtype = {torch.complex64: C64, torch.complex128: C128}.get(t.dtype)
+        if dtype is None:
+            raise QCError(QC_ERR_ARG, "tensor dtype must be complex64 or complex128")
+        n = int(t.numel()).bit_length() - 1
+        if (1 << n) != t.numel():
+            raise QCError(QC_ERR_ARG, "tensor size is not a power of two")
+        h = ctypes.c_void_p()
+        _check(lib.qc_state_wrap(ctypes.c_void_p(t.data_ptr()), n, dtype, ctypes.byref(h)))
+        return cls(n, dtype, handle=h, tensor=t)
+
+    def free(self):
+        if self._h is not None:
+            _check(lib.qc_state_free(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) is not None:
+                lib.qc_state_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def np_dtype(self):
+        return np.complex64 if self.dtype == C64 else np.complex128
+
+    def set_stream(self, stream):
+        """Bind a torch.cuda.Stream (or a raw cudaStream_t int / None)."""
+        raw = getattr(stream, "cuda_stream", stream)
+        _check(lib.qc_set_stream(self._h, ctypes.c_void_p(raw or 0)))
+
+    def set_arith(self, arith: int):
+        _check(lib.qc_set_arith(self._h, arith))
+
+    def set_basis(self, x: int = 0):
+        _check(lib.qc_state_set_basis(self._h, ctypes.c_uint64(x)))
+
+    def to_numpy(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(1 << self.n, dtype=self.np_dtype)
+        _check(lib.qc_state_copy_to_host(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def from_numpy(self, a):
+        a = np.ascontiguousarray(a, dtype=self.np_dtype)
+        assert a.size == (1 << self.n)
+        _check(lib.qc_state_copy_from_host(self._h, ctypes.c_void_p(a.ctypes.data)))
+        self._host_keep = a
+
+    def device_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        _check(lib.qc_state_info(self._h, ctypes.byref(p), None, None))
+        return p.value
+
+    # gates ---------------------------------------------------------------
+    def apply_1q(self, U, target: int):
+        m = _mat(U)
+        _check(lib.qc_apply_1q(self._h, _dptr(m), int(target)))
+
+    def apply_c1q(self, U, controls, cstates, target: int):
+        m = _mat(U)
+        _check(lib.qc_apply_c1q(self._h, _dptr(m), _iarr(controls), _iarr(cstates), len(controls), int(target)))
+
+    def apply_2q(self, U4, q0: int, q1: int):
+        m = _mat(U4)
+        _check(lib.qc_apply_2q(self._h, _dptr(m), int(q0), int(q1)))
+
+    def apply_kq(self, U, qubits, controls=(), cstates=()):
+        m = _mat(U)
+        _check(lib.qc_apply_kq(self._h, _dptr(m), _iarr(qubits), len(qubits), _iarr(controls),
+                               _iarr(cstates or [1] * len(controls)), len(controls)))
+
+    def apply_circuit(self, gates, fuse_k: int = 0, use_graph: bool = False, time_gates: bool = False):
+        """Apply the gate list; returns (n_launches, per-launch ms or None)."""
+        arr, keep = gate_records(gates)
+        nl = ctypes.c_int(0)
+        ms = (ctypes.c_float * max(1, len(gates)))() if time_gates else None
+        o = qc_opts(int(fuse_k), int(bool(use_graph)),
+                    ctypes.cast(ms, ctypes.POINTER(ctypes.c_float)) if ms is not None else None,
+                    ctypes.pointer(nl))
+        _check(lib.qc_apply_circuit(self._h, arr, len(gates), ctypes.byref(o)))
+        del keep
+        return nl.value, (np.array(ms[:nl.value], dtype=np.float64) if ms is not None else None)
+
+    def expect(self, hamiltonian) -> float:
+        rec, keep = pauli_record(hamiltonian)
+        out = ctypes.c_double(0.0)
+        _check(lib.qc_expect(self._h, ctypes.byref(rec), ctypes.byref(out)))
+        del keep
+        return out.value
+
+
+def fuse_plan(n: int, gates, fuse_k: int):
+    """Host-only launch plan: list of (qubits, controls, cstates, U) blocks."""
+    arr, keep = gate_records(gates)
+    nb = ctypes.c_int(0)
+    cap = max(1, len(gates))
+    blocks = (qc_block * cap)()
+    _check(lib.qc_fuse_plan(n, arr, len(gates), int(fuse_k), blocks, cap, ctypes.byref(nb)))
+    out = []
+    for b in blocks[:nb.value]:
+        d = 1 << b.k
+        U = np.array(b.U[:2 * d * d], dtype=np.float64).view(np.complex128).reshape(d, d)
+        out.append((tuple(b.qubits[:b.k]), tuple(b.controls[:b.nc]), tuple(b.cstates[:b.nc]), U.copy()))
+    del keep
+    return out
+
+
+def version() -> str:
+    return lib.qc_version().decode()

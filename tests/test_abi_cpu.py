@@ -1,0 +1,95 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+function declared in include/qcgb300.h; argument validation; and the host-side
+fusion planner, pinned through the FP64 oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2303_00123_gb300 import build
+    build.build()
+    from paper_2303_00123_gb300 import qcgb300
+    return qcgb300
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "qcgb300.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(qc_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(q):
+    names = declared_functions()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(q.lib, name), name
+    assert q.version().startswith("qcgb300")
+
+
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def test_argument_validation_without_gpu(q):
+    h = ctypes.c_void_p()
+    assert q.lib.qc_state_alloc(0, q.C128, ctypes.byref(h)) == q.QC_ERR_ARG
+    assert q.lib.qc_state_alloc(5, 7, ctypes.byref(h)) == q.QC_ERR_ARG
+    assert q.lib.qc_state_alloc(5, q.C128, None) == q.QC_ERR_ARG
+    assert q.lib.qc_state_free(None) == q.QC_OK
+    assert q.lib.qc_apply_1q(None, None, 0) == q.QC_ERR_ARG
+    assert b"NULL" in q.lib.qc_last_error()
+    if not _has_gpu():
+        # no device: a valid request fails cleanly with QC_ERR_CUDA, no fallback
+        assert q.lib.qc_state_alloc(5, q.C128, ctypes.byref(h)) == q.QC_ERR_CUDA
+
+
+def test_fuse_plan_rejects_bad_gates(q):
+    from paper_2303_00123_gb300.circuits import Gate
+    with pytest.raises(q.QCError):
+        q.fuse_plan(3, [Gate("H", (3,))], 0)
+    with pytest.raises(q.QCError):
+        q.fuse_plan(3, [Gate("X", (1,), controls=(1,))], 0)
+    with pytest.raises(q.QCError):
+        q.fuse_plan(3, [Gate("H", (0,))], 6)
+
+
+@pytest.mark.parametrize("fuse_k", [0, 2, 3, 4, 5])
+def test_fusion_plan_reproduces_the_circuit(q, fuse_k):
+    """Applying the planned blocks with the oracle equals applying the original
+    gates with the oracle (fusion may only change rounding)."""
+    from oracle import oracle as O
+    from paper_2303_00123_gb300 import circuits as C
+    n = 7
+    gates = C.random_mix(n, 120, seed=11) + C.qft(n) + C.brickwork(n, 4, seed=12)
+    gates += [C.Gate("X", (2,), controls=(0, 5), cstates=(1, 0)), C.Gate("RZ", (3,), theta=0.3)]
+    plan = q.fuse_plan(n, gates, fuse_k)
+    if fuse_k >= 2:
+        assert len(plan) < (0.6 if fuse_k == 2 else 0.35) * len(gates)
+        assert max(len(b[0]) + len(b[1]) for b in plan) <= max(fuse_k, 3)
+    else:
+        assert len(plan) == len(gates)
+    phi = C.random_state(n, 13)
+    ref = O.run_circuit(n, gates, phi)
+    psi = phi.copy()
+    for qubits, controls, cstates, U in plan:
+        O.apply_matrix(psi, n, U, qubits, controls, cstates)
+    np.testing.assert_allclose(psi, ref, atol=1e-12)
+
+
+def test_fusion_of_brickwork_reduces_sweeps(q):
+    from paper_2303_00123_gb300 import circuits as C
+    g = C.brickwork(30, 40, seed=0)
+    counts = {k: len(q.fuse_plan(30, g, k)) for k in (0, 2, 3, 4, 5)}
+    assert counts[0] == 1780
+    assert counts[5] < counts[4] < counts[3] < counts[2] < counts[0]
