@@ -275,6 +275,62 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def case_gates(kind, n, rng):
+    """One gate per target position for the --case micro-benchmarks."""
+    gates = []
+    for t in range(n):
+        if kind == "dense1q":
+            gates.append(C.Gate("U", (t,), matrix=C.haar_unitary(rng, 2)))
+        elif kind == "cnot":
+            gates.append(C.Gate("X", (t,), controls=((t + 1) % n,)))
+        elif kind == "cphase":
+            gates.append(C.Gate("P", (t,), controls=((t + 7) % n,), theta=0.3))
+        elif kind == "dense2q":
+            gates.append(C.Gate("U4", (t, (t + 1) % n), matrix=C.haar_unitary(rng, 4)))
+        elif kind == "swap":
+            gates.append(C.Gate("SWAP", (t, (t + n // 2) % n)))
+        elif kind == "h":
+            gates.append(C.Gate("H", (t,)))
+        else:
+            raise SystemExit("unknown case " + kind)
+    return gates
+
+
+def run_case(args):
+    """Per-target-qubit timing of one gate kind on an n-qubit state."""
+    import torch
+    from paper_2303_00123_gb300 import qcgb300 as q
+    n = args.n
+    dt = q.C64 if args.dtype == "c64" else q.C128
+    elem = 8 if dt == q.C64 else 16
+    t = torch.zeros(1 << n, dtype=torch.complex64 if dt == q.C64 else torch.complex128, device="cuda")
+    st = q.State.from_tensor(t)
+    st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
+    stream = torch.cuda.Stream()
+    st.set_stream(stream)
+    st.set_basis(0)
+    gates = case_gates(args.case, n, np.random.default_rng(7))
+    for _ in range(args.warmup):
+        st.apply_circuit(gates)
+    per = np.zeros(len(gates))
+    for _ in range(args.steps):
+        _, ms = st.apply_circuit(gates, time_gates=True)
+        per += ms
+    per /= max(1, args.steps)
+    out = []
+    for g, m in zip(gates, per):
+        b = algorithmic_bytes(g, n, elem)
+        out.append({"q": g.qubits[0], "stride": 1 << (n - 1 - g.qubits[0]), "ms": round(float(m), 4),
+                    "GBps": round(b / (m * 1e-3) / 1e9, 1)})
+    peak, _ = measured_peaks()
+    tot_b = sum(algorithmic_bytes(g, n, elem) for g in gates)
+    print(json.dumps({"case": args.case, "n": n, "dtype": args.dtype, "arith": args.arith,
+                      "avg_GBps": round(tot_b / (per.sum() * 1e-3) / 1e9, 1),
+                      "frac_of_measured_hbm": round(tot_b / (per.sum() * 1e-3) / 1e9 / peak, 4),
+                      "per_target": out}))
+    st.free()
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -315,8 +371,13 @@ def main():
     ap.add_argument("--fuse", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", default=None, help="micro-benchmark: dense1q, dense2q, cnot, cphase, swap, h")
+    ap.add_argument("--n", type=int, default=28)
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

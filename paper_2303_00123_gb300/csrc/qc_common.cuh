@@ -158,9 +158,9 @@ struct ArC128 {
 // two float parts (converted to doubles by integer bit operations) with a
 // single FP64 add -- the only FP64-pipe instruction per output.
 //
-// Accuracy: the split keeps the leading 47 significand bits of each input
-// (relative error < 2^-46); each real output carries an error of about
-// 2^-46 * sum_k |u_k| |x_k|.  Range: inputs with |x| < 2^-100 are flushed to
+// Accuracy: the split keeps each input to 47 significant bits, rounded to
+// nearest (relative error <= 2^-47, unbiased); each real output carries an
+// error of about 2^-46 * sum_k |u_k| |x_k|.  Range: inputs with |x| < 2^-100 are flushed to
 // zero (absolute error < 1e-30); |x| must stay below 2^127.
 struct ArC128x {
   static constexpr int V = 2;
@@ -182,11 +182,15 @@ struct ArC128x {
     const uint32_t t = w1 - 0x38000000u;
     uint32_t h = __funnelshift_l(w0, t, 3);
     h = (h & 0x7FFFFFFFu) | (w1 & 0x80000000u);
-    // lo: the next 23 mantissa bits m (w0 bits 28..6) weigh 2^(E-46); the
-    // float difference (1.m * 2^(E-23)) - 2^(E-23) is exact and equals that.
+    // lo: the remaining 29 mantissa bits (w0 bits 28..0), rounded to the
+    // nearest multiple of 2^6 units, i.e. m * 2^(E-46) with m <= 2^23; the
+    // float difference (base + m) - base, with base = 2^(E-23), is exact and
+    // equals that (an m of 2^23 carries into the exponent, still exact).
+    // Rounding (not truncating) keeps the split unbiased: x is represented
+    // to 47 significant bits, |x - (hi + lo)| <= 2^-47 |x|.
     const uint32_t base = (h & 0xFF800000u) - 0x0B800000u;
-    const uint32_t f1 = ((w0 >> 6) & 0x007FFFFFu) | base;
-    const float lo = __uint_as_float(f1) - __uint_as_float(base);
+    const uint32_t m = ((w0 & 0x1FFFFFFFu) + 32u) >> 6;
+    const float lo = __uint_as_float(base + m) - __uint_as_float(base);
     const bool tiny = (w1 & 0x7FFFFFFFu) < 0x39B00000u;  // |x| < 2^-100, or 0
     ff r;
     r.h = tiny ? 0.f : __uint_as_float(h);

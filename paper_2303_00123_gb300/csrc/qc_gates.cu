@@ -458,8 +458,9 @@ template <class Ar>
 int dispatch(qc_state* s, qc_op op) {
   constexpr int L = Ar::V == 4 ? 2 : 1;
   const int E = Ar::E;
-  // Very small states (a single vector or less) and wide gates use k_kq.
-  if (op.k >= 3 || s->n < 5) return launch_kq<Ar>(s, op);
+  // Wide gates (k >= 3) and states smaller than one 32-byte vector use k_kq.
+  const bool tiny = s->n < L;
+  if (op.k >= 3) return launch_kq<Ar>(s, op);
   order_two_qubit(op);
   const double* U = op.U;
   const int D = 1 << op.k;
@@ -473,7 +474,7 @@ int dispatch(qc_state* s, qc_op op) {
     for (int r = 0; r < D; r++)
       if (!cis(&U[2 * (r * D + r)], 1.0, 0.0)) { nonone++; which = r; }
     if (nonone == 0) return QC_OK;  // identity
-    if (nonone == 1) {
+    if (nonone == 1 && !tiny) {
       // Restricted phase: the targets act as extra controls with the bit
       // pattern of the one diagonal entry that differs from 1.
       int cpos[QC_MAX_CONTROLS + 2], cval[QC_MAX_CONTROLS + 2], nc = 0;
@@ -483,6 +484,7 @@ int dispatch(qc_state* s, qc_op op) {
       return launch_phase<Ar>(s, P, &U[2 * (which * D + which)]);
     }
   }
+  if (tiny) return launch_kq<Ar>(s, op);
   if (int rc = build_geom(s, L, op.tpos, op.k, op.cpos, op.cval, op.nc, P)) return rc;
   if (op.k == 1 && cis(&U[0], 0, 0) && cis(&U[2], 1, 0) && cis(&U[4], 1, 0) && cis(&U[6], 0, 0))
     return E == 16 ? launch_perm<16, 0>(s, P) : launch_perm<8, 0>(s, P);

@@ -128,8 +128,10 @@ def one_gate_cases(n, rng):
                 g.append(Gate("U4", (a, b), matrix=rand_u(rng, 4)))
                 g.append(Gate("SWAP", (a, b)))
     diag = np.diag(np.exp(1j * rng.uniform(-3, 3, size=4)))
-    g.append(Gate("U4", (0, n - 1), matrix=diag))
-    g.append(Gate("U4", (n - 1, 1), matrix=np.diag([1, 1, 1, np.exp(0.7j)])))
+    if n >= 2:
+        g.append(Gate("U4", (0, n - 1), matrix=diag))
+    if n >= 3:
+        g.append(Gate("U4", (n - 1, 1), matrix=np.diag([1, 1, 1, np.exp(0.7j)])))
     for k in (3, 4, 5):
         if k <= n:
             qs = [int(v) for v in rng.choice(n, size=k, replace=False)]
