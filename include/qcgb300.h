@@ -212,6 +212,37 @@ typedef struct {
  * modified. */
 int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out);
 
+/* ---- gradients ------------------------------------------------------------
+ * Adjoint (reverse-sweep) gradients of E(theta) = <psi(theta)| H |psi(theta)>,
+ * |psi(theta)> = U_L ... U_1 |0...0>, for every parametric gate
+ * U_l = exp(-i theta_l P_l / 2) (RX, RY, RZ without controls; P_l = X, Y, Z):
+ *   dE/dtheta_l = Im <lambda_l| P_l |phi_l>,
+ *   phi_l = U_l ... U_1 |0>,  lambda_l = U_{l+1}^dag ... U_L^dag H |psi>
+ * (Jones & Gacon 2020, arXiv:2009.02823).  The library keeps two states per
+ * parameter set (phi and lambda), walks the circuit backwards once, and fuses
+ * each parametric gate's reduction with undoing that gate on both states.
+ * Reductions (energy, gradients) accumulate in FP64 on the device.
+ *
+ * gates/ngates: the circuit (gates with k <= 2 targets; any controls).
+ * thetas: host [batch][nparams], nparams = number of parametric gates, in
+ *   circuit order; NULL means "use each gate's own theta" (batch must be 1).
+ * energies: host [batch] out; grads: host [batch][nparams] out.
+ * dtype: QC_C64 (FP32 sweeps, FP64 reductions) or QC_C128 (arith as in
+ *   qc_arith).  stream: cudaStream_t or NULL.  Device workspace: 2 * batch
+ *   states plus partial sums, allocated on the first call and reused (it grows
+ *   when a larger problem arrives).  Synchronises the stream. */
+typedef struct {
+  int dtype;
+  int arith;
+  void* stream;
+} qc_grad_opts;
+
+int qc_adjoint_grad(int n, const qc_gate* gates, int ngates, const double* thetas, int batch,
+                    const qc_pauli_sum* H, double* energies, double* grads, const qc_grad_opts* opts);
+
+/* Number of parametric gates (RX/RY/RZ without controls) in a gate list. */
+int qc_count_params(const qc_gate* gates, int ngates, int* nparams);
+
 /* ---- diagnostics ---------------------------------------------------------- */
 /* Message of the last failing call on this thread ("" if none). */
 const char* qc_last_error(void);

@@ -239,6 +239,13 @@ void fuse(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Emitt
 
 }  // namespace
 
+int qc_gate_to_op(int n, const qc_gate& g, qc_op& op) {
+  Resolved R;
+  if (int rc = resolve(n, g, R)) return rc;
+  to_op(n, R, op);
+  return QC_OK;
+}
+
 namespace {
 // Build the launch plan (shared by qc_apply_circuit and qc_fuse_plan).
 int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops) {

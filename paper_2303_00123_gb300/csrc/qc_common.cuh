@@ -101,6 +101,9 @@ struct ArC64 {
   struct val_t { float re, im; };
   struct coef_t { float re, im; };
   static __host__ coef_t make_coef(double re, double im) { return {(float)re, (float)im}; }
+  using raw_t = float2;
+  static __device__ __forceinline__ val_t from_raw(const raw_t& r) { return {r.x, r.y}; }
+  static __device__ __forceinline__ raw_t to_raw(const val_t& x) { return make_float2(x.re, x.im); }
   static __device__ __forceinline__ val_t load(const vec32& v, int e) {
     return {__uint_as_float(v.w[2 * e]), __uint_as_float(v.w[2 * e + 1])};
   }
@@ -126,6 +129,9 @@ struct ArC128 {
   struct val_t { double re, im; };
   struct coef_t { double re, im; };
   static __host__ coef_t make_coef(double re, double im) { return {re, im}; }
+  using raw_t = double2;
+  static __device__ __forceinline__ val_t from_raw(const raw_t& r) { return {r.x, r.y}; }
+  static __device__ __forceinline__ raw_t to_raw(const val_t& x) { return make_double2(x.re, x.im); }
   static __device__ __forceinline__ val_t load(const vec32& v, int e) {
     return {__hiloint2double((int)v.w[4 * e + 1], (int)v.w[4 * e]),
             __hiloint2double((int)v.w[4 * e + 3], (int)v.w[4 * e + 2])};
@@ -209,6 +215,14 @@ struct ArC128x {
   static __device__ __forceinline__ val_t load(const vec32& v, int e) {
     return {split(v.w[4 * e], v.w[4 * e + 1]), split(v.w[4 * e + 2], v.w[4 * e + 3])};
   }
+  using raw_t = double2;
+  static __device__ __forceinline__ val_t from_raw(const raw_t& r) {
+    return {split((uint32_t)__double2loint(r.x), (uint32_t)__double2hiint(r.x)),
+            split((uint32_t)__double2loint(r.y), (uint32_t)__double2hiint(r.y))};
+  }
+  static __device__ __forceinline__ raw_t to_raw(const val_t& x) {
+    return make_double2(f2d(x.re.h) + f2d(x.re.l), f2d(x.im.h) + f2d(x.im.l));
+  }
   // x holds unnormalised (s, c) pairs; the double is s + c rounded once.
   static __device__ __forceinline__ void store(vec32& v, int e, const val_t& x) {
     const double re = f2d(x.re.h) + f2d(x.re.l);
@@ -272,6 +286,10 @@ struct qc_op {
   int cval[QC_MAX_CONTROLS];    // control states
   double U[2 * 32 * 32];        // 2^k x 2^k complex, row-major (re, im)
 };
+
+// Resolve a gate record (named or explicit matrix) into an op: validates the
+// qubits, builds the matrix (host FP64) and converts qubits to bit positions.
+int qc_gate_to_op(int n, const qc_gate& g, qc_op& op);
 
 // Apply one (controlled) k-qubit gate given by its matrix; the launcher
 // classifies the matrix (dense / permutation / diagonal) and picks a kernel.

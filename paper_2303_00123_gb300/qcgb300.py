@@ -48,6 +48,10 @@ class qc_block(ctypes.Structure):
                 ("U", ctypes.c_double * (2 * 32 * 32))]
 
 
+class qc_grad_opts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("arith", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
 class qc_pauli_sum(ctypes.Structure):
     _fields_ = [("nterms", ctypes.c_int), ("coeffs", ctypes.POINTER(ctypes.c_double)),
                 ("offsets", ctypes.POINTER(ctypes.c_int)), ("letters", ctypes.c_char_p),
@@ -80,6 +84,9 @@ def _load():
         "qc_apply_circuit": [P, ctypes.POINTER(qc_gate), I, ctypes.POINTER(qc_opts)],
         "qc_expect": [P, ctypes.POINTER(qc_pauli_sum), DP],
         "qc_fuse_plan": [I, ctypes.POINTER(qc_gate), I, I, ctypes.POINTER(qc_block), I, IP],
+        "qc_adjoint_grad": [I, ctypes.POINTER(qc_gate), I, DP, I, ctypes.POINTER(qc_pauli_sum), DP, DP,
+                            ctypes.POINTER(qc_grad_opts)],
+        "qc_count_params": [ctypes.POINTER(qc_gate), I, IP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -294,6 +301,38 @@ def fuse_plan(n: int, gates, fuse_k: int):
         out.append((tuple(b.qubits[:b.k]), tuple(b.controls[:b.nc]), tuple(b.cstates[:b.nc]), U.copy()))
     del keep
     return out
+
+
+def count_params(gates) -> int:
+    arr, keep = gate_records(gates)
+    c = ctypes.c_int(0)
+    _check(lib.qc_count_params(arr, len(gates), ctypes.byref(c)))
+    return c.value
+
+
+def adjoint_grad(n: int, gates, hamiltonian, thetas=None, dtype: int = C128, arith: int = ARITH_AUTO,
+                 stream=None):
+    """Energies [B] and adjoint gradients [B, P] of the parametric gates
+    (RX/RY/RZ without controls).  thetas: None (use the gates' own angles) or
+    an array [B, P] of angles for the parametric gates in circuit order."""
+    arr, keep = gate_records(gates)
+    P = count_params(gates)
+    if thetas is None:
+        B = 1
+        th = None
+    else:
+        th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(-1, P) if P else
+                                  np.zeros((np.asarray(thetas).shape[0], 0)))
+        B = th.shape[0]
+    rec, hk = pauli_record(hamiltonian)
+    e = np.zeros(B, dtype=np.float64)
+    g = np.zeros((B, max(P, 1)), dtype=np.float64)
+    raw = getattr(stream, "cuda_stream", stream)
+    o = qc_grad_opts(int(dtype), int(arith), ctypes.c_void_p(raw or 0))
+    _check(lib.qc_adjoint_grad(n, arr, len(gates), _dptr(th) if th is not None and th.size else None, B,
+                               ctypes.byref(rec), _dptr(e), _dptr(g), ctypes.byref(o)))
+    del keep, hk
+    return e, g[:, :P]
 
 
 def version() -> str:

@@ -93,3 +93,12 @@ def test_fusion_of_brickwork_reduces_sweeps(q):
     counts = {k: len(q.fuse_plan(30, g, k)) for k in (0, 2, 3, 4, 5)}
     assert counts[0] == 1780
     assert counts[5] < counts[4] < counts[3] < counts[2] < counts[0]
+
+
+def test_count_params(q):
+    from paper_2303_00123_gb300 import circuits as C
+    n, layers = 5, 3
+    gates = C.hea(n, layers, C.hea_thetas(n, layers, seed=1))
+    assert q.count_params(gates) == 2 * n * layers
+    gates.append(C.Gate("RZ", (1,), controls=(2,), theta=0.3))   # controlled: not a parameter
+    assert q.count_params(gates) == 2 * n * layers
