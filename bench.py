@@ -296,10 +296,40 @@ def case_gates(kind, n, rng):
     return gates
 
 
+def run_adjoint_case(args):
+    """Adjoint gradients of the hardware-efficient ansatz (n qubits, 10
+    layers of RY, RZ and a CNOT ladder, 2*n*10 parameters) for the TFIM chain,
+    a batch of parameter sets per call; reports gradient sets per second."""
+    import torch
+    from paper_2303_00123_gb300 import qcgb300 as q
+    n, layers, B = args.n, 10, args.batch
+    th = C.hea_thetas(n, layers, seed=2025, batch=B)
+    gates = C.hea(n, layers, th[0])
+    H = C.tfim(n, 1.0)
+    dt = q.C64 if args.dtype == "c64" else q.C128
+    ar = q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE
+    for _ in range(args.warmup):
+        q.adjoint_grad(n, gates, H, th, dtype=dt, arith=ar)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e, g = q.adjoint_grad(n, gates, H, th, dtype=dt, arith=ar)
+    dt_s = (time.perf_counter() - t0) / args.steps
+    state_bytes = (1 << n) * (8 if dt == q.C64 else 16)
+    nparam = g.shape[1]
+    print(json.dumps({"case": "adjoint", "n": n, "layers": layers, "batch": B, "params": nparam,
+                      "dtype": args.dtype, "arith": args.arith, "s_per_call": round(dt_s, 4),
+                      "gradient_sets_per_s": round(B / dt_s, 2),
+                      "param_grads_per_s": round(B * nparam / dt_s, 1),
+                      "workspace_bytes": 2 * B * state_bytes}))
+
+
 def run_case(args):
     """Per-target-qubit timing of one gate kind on an n-qubit state."""
     import torch
     from paper_2303_00123_gb300 import qcgb300 as q
+    if args.case == "adjoint":
+        return run_adjoint_case(args)
     n = args.n
     dt = q.C64 if args.dtype == "c64" else q.C128
     elem = 8 if dt == q.C64 else 16
@@ -374,6 +404,7 @@ def main():
     ap.add_argument("--case", default=None, help="micro-benchmark: dense1q, dense2q, cnot, cphase, swap, h")
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--batch", type=int, default=64)
     args = ap.parse_args()
     if args.case:
         run_case(args)
