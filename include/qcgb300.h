@@ -212,6 +212,24 @@ typedef struct {
  * modified. */
 int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out);
 
+/* Same result as qc_expect, for callers that cannot allocate device memory
+ * -- for instance an application whose own memory manager (a framework's
+ * caching allocator) has already reserved the whole device, or a
+ * latency-critical loop in which a cudaMalloc, which may synchronise the
+ * device, is not acceptable.  This entry point allocates nothing: its
+ * partial sums live in a fixed array inside the library's device code
+ * (4096 + 1024 doubles, about 40 KB, held on every device that loads the
+ * library until the process exits).  The paper has no counterpart; this is an
+ * interface choice of this library.
+ * Limit: at most 1023 sweeps, one per distinct X/Y pattern of the terms per
+ * 64 terms; larger sums return QC_ERR_ARG before any work is enqueued.
+ * The first call on a device looks the array's device address up (with that
+ * device current); make that first call before any stream capture.  Every
+ * call uses the same array, so calls that overlap on the GPU (other threads,
+ * other streams) race; calls from several host threads are serialised by the
+ * library.  Synchronises the state's stream. */
+int qc_expect_noalloc(const qc_state* s, const qc_pauli_sum* H, double* out);
+
 /* ---- gradients ------------------------------------------------------------
  * Adjoint (reverse-sweep) gradients of E(theta) = <psi(theta)| H |psi(theta)>,
  * |psi(theta)> = U_L ... U_1 |0...0>, for every parametric gate

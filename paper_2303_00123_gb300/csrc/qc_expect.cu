@@ -212,3 +212,150 @@ extern "C" int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out) 
   *out = result;
   return QC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// qc_expect_noalloc: the same sweeps and reductions as qc_expect, with the
+// partial sums held in a fixed device array instead of a heap buffer.
+// Layout of the array: [kNaPartials partials of the current sweep]
+// [kNaSweeps per-sweep sums][1 final sum].  Each call writes every slot it
+// later reads, so nothing has to be cleared between calls.
+namespace {
+constexpr int kNaPartials = 4096;   // blocks per sweep (grid is capped at this)
+constexpr int kNaSweeps = 1023;     // distinct X/Y patterns (64 terms per sweep)
+static __device__ __align__(256) double g_na_scratch[kNaPartials + kNaSweeps + 1];
+
+std::mutex g_na_mu;
+double* g_na_ptr[64] = {nullptr};   // device address of g_na_scratch, per device
+
+int na_setup(int dev, double** p) {
+  if (dev < 0 || dev >= 64) return qc_fail(QC_ERR_UNSUPPORTED, "device ordinal %d >= 64", dev);
+  if (!g_na_ptr[dev]) {
+    void* a = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_na_scratch);   // the state's device is current
+    if (e != cudaSuccess) return qc_cuda_fail(e, "cudaGetSymbolAddress(g_na_scratch)");
+    g_na_ptr[dev] = (double*)a;
+  }
+  *p = g_na_ptr[dev];
+  return QC_OK;
+}
+
+// Flip and phase masks of term t (validated); returns QC_OK or an error.
+int na_term(int n, const qc_pauli_sum* H, int t, uint64_t* F, uint64_t* Q, int* ny) {
+  const int b = H->offsets[t], e = H->offsets[t + 1];
+  if (e < b) return qc_fail(QC_ERR_ARG, "term %d: offsets decrease", t);
+  if (e > b && (!H->letters || !H->qubits)) return qc_fail(QC_ERR_ARG, "Pauli letters/qubits are NULL");
+  uint64_t f = 0, q = 0, used = 0;
+  int y = 0;
+  for (int i = b; i < e; i++) {
+    const int qb = H->qubits[i];
+    if (qb < 0 || qb >= n) return qc_fail(QC_ERR_ARG, "term %d: qubit %d out of range", t, qb);
+    const uint64_t bit = 1ull << (n - 1 - qb);
+    const char L = H->letters[i];
+    if (L == 'I' || L == 'i') continue;
+    if (used & bit) return qc_fail(QC_ERR_ARG, "term %d: qubit %d appears twice", t, qb);
+    used |= bit;
+    if (L == 'X' || L == 'x') f |= bit;
+    else if (L == 'Y' || L == 'y') { f |= bit; q |= bit; y++; }
+    else if (L == 'Z' || L == 'z') q |= bit;
+    else return qc_fail(QC_ERR_ARG, "term %d: unknown Pauli letter '%c'", t, L);
+  }
+  *F = f;
+  *Q = q;
+  *ny = y;
+  return QC_OK;
+}
+}  // namespace
+
+extern "C" int qc_expect_noalloc(const qc_state* s, const qc_pauli_sum* H, double* out) {
+  if (int rc = qc_check_state(s)) return rc;
+  if (!out) return qc_fail(QC_ERR_ARG, "out is NULL");
+  if (!H || H->nterms < 0) return qc_fail(QC_ERR_ARG, "invalid Pauli sum");
+  if (H->nterms > 0 && (!H->coeffs || !H->offsets)) return qc_fail(QC_ERR_ARG, "Pauli sum arrays are NULL");
+  // Validate every term and count the sweeps before touching the device.
+  int nsweeps = 0;
+  for (int t = 0; t < H->nterms; t++) {
+    uint64_t F, Q;
+    int ny;
+    if (int rc = na_term(s->n, H, t, &F, &Q, &ny)) return rc;
+    bool seen = false;
+    for (int u = 0; u < t && !seen; u++) {
+      uint64_t F2, Q2;
+      int ny2;
+      na_term(s->n, H, u, &F2, &Q2, &ny2);
+      seen = (F2 == F);
+    }
+    if (seen) continue;
+    int cnt = 0;
+    for (int u = t; u < H->nterms; u++) {
+      uint64_t F2, Q2;
+      int ny2;
+      na_term(s->n, H, u, &F2, &Q2, &ny2);
+      if (F2 == F) cnt++;
+    }
+    nsweeps += (cnt + kMaxTermsPerSweep - 1) / kMaxTermsPerSweep;
+  }
+  if (nsweeps > kNaSweeps)
+    return qc_fail(QC_ERR_ARG, "qc_expect_noalloc: %d sweeps needed, the fixed scratch holds at most %d "
+                   "(distinct X/Y patterns, 64 terms per sweep)", nsweeps, kNaSweeps);
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  double* scratch = nullptr;
+  if (int rc = na_setup(s->device, &scratch)) return rc;
+  double* partial = scratch;
+  double* sweep_sum = scratch + kNaPartials;
+  double* final_sum = sweep_sum + kNaSweeps;
+  const uint64_t N = 1ull << s->n;
+  const int cap = std::min(qc_num_sms() * 8, kNaPartials);
+  int sw = 0;
+  for (int t = 0; t < H->nterms; t++) {
+    uint64_t F, Q;
+    int ny;
+    na_term(s->n, H, t, &F, &Q, &ny);
+    bool seen = false;
+    for (int u = 0; u < t && !seen; u++) {
+      uint64_t F2, Q2;
+      int ny2;
+      na_term(s->n, H, u, &F2, &Q2, &ny2);
+      seen = (F2 == F);
+    }
+    if (seen) continue;
+    TermSet ts;
+    std::memset(&ts, 0, sizeof(ts));
+    ts.flip = F;
+    ts.pivot = F ? 63 - __builtin_clzll(F) : -1;
+    const uint64_t npairs = F ? N / 2 : N;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((npairs + kThreads - 1) / kThreads, cap));
+    for (int u = t; u <= H->nterms; u++) {
+      bool flush = (u == H->nterms);
+      if (!flush) {
+        uint64_t F2, Q2;
+        int ny2;
+        na_term(s->n, H, u, &F2, &Q2, &ny2);
+        if (F2 != F) continue;
+        ts.phase_mask[ts.nterms] = Q2;
+        ts.coeff[ts.nterms] = H->coeffs[u];
+        ts.ipow[ts.nterms] = ny2 & 3;
+        ts.nterms++;
+        flush = (ts.nterms == kMaxTermsPerSweep);
+      }
+      if (flush && ts.nterms > 0) {
+        if (s->dtype == QC_C64)
+          k_pauli_sweep<float2><<<grid, kThreads, 0, s->stream>>>((const float2*)s->ptr, npairs, ts, partial);
+        else
+          k_pauli_sweep<double2><<<grid, kThreads, 0, s->stream>>>((const double2*)s->ptr, npairs, ts, partial);
+        k_sum_partials<<<1, kThreads, 0, s->stream>>>(partial, grid, sweep_sum + sw);
+        QC_LAUNCHED("qc_expect_noalloc sweep");
+        sw++;
+        ts.nterms = 0;
+      }
+    }
+  }
+  double result = 0.0;
+  if (sw > 0) {
+    k_sum_partials<<<1, kThreads, 0, s->stream>>>(sweep_sum, sw, final_sum);
+    QC_LAUNCHED("qc_expect_noalloc final sum");
+    QC_CUDA(cudaMemcpyAsync(&result, final_sum, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  }
+  QC_CUDA(cudaStreamSynchronize(s->stream));
+  *out = result;
+  return QC_OK;
+}

@@ -83,6 +83,7 @@ def _load():
         "qc_apply_kq": [P, DP, IP, I, IP, IP, I],
         "qc_apply_circuit": [P, ctypes.POINTER(qc_gate), I, ctypes.POINTER(qc_opts)],
         "qc_expect": [P, ctypes.POINTER(qc_pauli_sum), DP],
+        "qc_expect_noalloc": [P, ctypes.POINTER(qc_pauli_sum), DP],
         "qc_fuse_plan": [I, ctypes.POINTER(qc_gate), I, I, ctypes.POINTER(qc_block), I, IP],
         "qc_adjoint_grad": [I, ctypes.POINTER(qc_gate), I, DP, I, ctypes.POINTER(qc_pauli_sum), DP, DP,
                             ctypes.POINTER(qc_grad_opts)],
@@ -283,6 +284,14 @@ class State:
         rec, keep = pauli_record(hamiltonian)
         out = ctypes.c_double(0.0)
         _check(lib.qc_expect(self._h, ctypes.byref(rec), ctypes.byref(out)))
+        del keep
+        return out.value
+
+    def expect_noalloc(self, hamiltonian) -> float:
+        """qc_expect_noalloc: same value, no device allocation (fixed scratch)."""
+        rec, keep = pauli_record(hamiltonian)
+        out = ctypes.c_double(0.0)
+        _check(lib.qc_expect_noalloc(self._h, ctypes.byref(rec), ctypes.byref(out)))
         del keep
         return out.value
 
