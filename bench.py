@@ -324,12 +324,69 @@ def run_adjoint_case(args):
                       "workspace_bytes": 2 * B * state_bytes}))
 
 
+def run_batch_case(args):
+    """1024 independent random circuits (n ~ U[10,24], depth ~ U[50,300],
+    complex64) in one persistent launch (autotuned fusion, graph replay)
+    against one circuit after another with one launch per gate."""
+    import torch
+    from paper_2303_00123_gb300 import qcgb300 as q
+    specs = C.batch_specs(args.batch, seed=4)
+    circs = [C.random_mix(n, d, seed=s) for n, d, s in specs]
+    ngates = sum(len(g) for g in circs)
+    dt = q.C64 if args.dtype == "c64" else q.C128
+    sts = [q.State(n, dt) for n, _, _ in specs]
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    b = q.Batch(sts, circs, fuse_k=args.fuse if args.fuse != 0 else -1, use_graph=True, stream=stream)
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        b.launch(timing=True)
+    tots, comps = [], []
+    for _ in range(args.steps):
+        comp, tot = b.launch(timing=True)
+        tots.append(tot)
+        comps.append(comp)
+    tot = float(np.median(tots))
+    comp = comps[int(np.argmin(np.abs(np.array(tots) - tot)))]
+    info = b.info()
+    b.free()
+    # baseline: one circuit after another, one launch per gate
+    for st in sts:
+        st.set_stream(stream)
+    base_comp = np.zeros(len(circs))
+    ev0 = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in circs]
+    for rep in range(2):                 # first pass warms up
+        ev0.record(stream)
+        for i, (st, g) in enumerate(zip(sts, circs)):
+            st.set_basis(0)
+            st.apply_circuit(g)
+            evs[i].record(stream)
+        stream.synchronize()
+    for i in range(len(circs)):
+        base_comp[i] = ev0.elapsed_time(evs[i])
+    base_tot = float(base_comp.max())
+    for st in sts:
+        st.free()
+    print(json.dumps({"case": "batch", "circuits": len(circs), "gates": ngates, "dtype": args.dtype,
+                      "fuse_k": info["fuse_k"], "ops": info["ops"], "smem_circuits": info["smem_circuits"],
+                      "persistent": {"ms": round(tot, 3), "gates_per_s": round(ngates / tot * 1e3, 1),
+                                     "p50_ms": round(float(np.percentile(comp, 50)), 3),
+                                     "p99_ms": round(float(np.percentile(comp, 99)), 3)},
+                      "one_launch_per_gate": {"ms": round(base_tot, 3), "gates_per_s": round(ngates / base_tot * 1e3, 1),
+                                              "p50_ms": round(float(np.percentile(base_comp, 50)), 3),
+                                              "p99_ms": round(float(np.percentile(base_comp, 99)), 3)},
+                      "speedup": round(base_tot / tot, 2), "autotune_s": round(tune_s, 2)}))
+
+
 def run_case(args):
     """Per-target-qubit timing of one gate kind on an n-qubit state."""
     import torch
     from paper_2303_00123_gb300 import qcgb300 as q
     if args.case == "adjoint":
         return run_adjoint_case(args)
+    if args.case == "batch":
+        return run_batch_case(args)
     n = args.n
     dt = q.C64 if args.dtype == "c64" else q.C128
     elem = 8 if dt == q.C64 else 16

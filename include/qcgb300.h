@@ -195,6 +195,44 @@ typedef struct {
 int qc_fuse_plan(int n, const qc_gate* gates, int ngates, int fuse_k,
                  qc_block* blocks, int max_blocks, int* nblocks);
 
+/* ---- batches of circuits -----------------------------------------------------
+ * Many independent circuits of different sizes and depths run in one
+ * persistent kernel launch (optionally captured in a CUDA graph and replayed).
+ * Each CTA takes circuits from an atomic work queue, largest first; a circuit
+ * whose state fits in the CTA's shared memory (complex64 n <= 13, complex128
+ * n <= 12) is simulated there from |0...0> and written to its state once;
+ * larger ones are swept in global memory by the CTA, gate block by gate block.
+ * CTAs never wait on one another.  Fusion (greedy, k <= 4) is applied per
+ * circuit; fuse_k < 0 lets the library time the candidates {1, 2, 3, 4} on the
+ * batch once and keep the fastest. */
+typedef struct {
+  int n;                 /* qubits of the circuit (must equal its state's n) */
+  int ngates;
+  const qc_gate* gates;  /* host memory, read during qc_batch_create only */
+} qc_circuit_desc;
+
+typedef struct {
+  int fuse_k;     /* -1: autotune; 0 or 1: gate by gate; 2..4: fusion width */
+  int use_graph;  /* 1: capture the launch in a CUDA graph, replayed by qc_batch_launch */
+  void* stream;   /* cudaStream_t or NULL */
+} qc_batch_opts;
+
+typedef struct qc_batch qc_batch;
+
+/* Plan a batch: states[i] (all of one dtype/arith, on one device) receives
+ * circuit i applied to |0...0> at every qc_batch_launch.  The plan owns its
+ * device tables; the states stay owned by the caller and must outlive it. */
+int qc_batch_create(qc_state* const* states, const qc_circuit_desc* circs, int ncirc,
+                    const qc_batch_opts* opts, qc_batch** out);
+/* Run the batch (asynchronous unless an output pointer is given).
+ * completion_ms: optional host [ncirc], time from the launch start to the end
+ * of each circuit (device clock); total_ms: optional, whole launch.  Either
+ * output synchronises the stream. */
+int qc_batch_launch(qc_batch* b, double* completion_ms, double* total_ms);
+/* Chosen fusion width and total number of ops (gates or fused blocks). */
+int qc_batch_info(const qc_batch* b, int* fuse_k, int* nops, int* nsmem_circuits);
+int qc_batch_free(qc_batch* b);
+
 /* ---- observables ---------------------------------------------------------
  * A Pauli sum H = sum_t coeffs[t] * P_t; term t consists of the (letter,
  * qubit) pairs with indices offsets[t] .. offsets[t+1]-1 of `letters`

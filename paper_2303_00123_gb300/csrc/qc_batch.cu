@@ -1,0 +1,394 @@
+// qc_batch.cu -- many independent circuits in one persistent launch.
+//
+// Host: every circuit is planned (resolved, optionally fused into blocks of
+// k <= 4 qubits) into ops {targets, controls, dense matrix}; all ops, matrices
+// and per-circuit records go to one device allocation.  Circuits are ordered by
+// work (2^n * ops), largest first.
+//
+// Device: a persistent kernel with as many CTAs as fit at once.  A CTA takes
+// the next circuit from an atomic queue and runs all of it:
+//   * shared-memory mode (state <= kSmemState bytes): the state is built as
+//     |0...0> in shared memory, every op is applied there (threads over the
+//     op's groups, __syncthreads between ops), and the final state is written
+//     to HBM once -- one pass over HBM for the whole circuit;
+//   * global mode: the state is initialised in place and swept op by op.
+// CTAs never wait on other CTAs (no inter-CTA barrier, no spin loop).
+// %globaltimer stamps give each circuit's completion time.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "qc_common.cuh"
+
+namespace {
+
+constexpr int kBT = 256;                 // threads per CTA
+constexpr int kMaxK = 4;                 // widest op (fused block)
+constexpr int kMaxD = 1 << kMaxK;
+constexpr size_t kSmemState = 64 * 1024; // bytes of shared memory for a state
+
+struct BOp {
+  uint32_t coef;      // first matrix entry in the coef table
+  uint8_t k;          // targets
+  uint8_t nins;       // inserted positions (targets + controls)
+  uint8_t tpos[kMaxK];
+  uint8_t ins[QC_MAX_INS];
+  uint64_t orval;     // control values
+};
+
+struct BCirc {
+  uint64_t state;     // device address of the state
+  uint32_t op0, nops; // op range
+  int n;
+  int smem;           // 1: shared-memory mode
+};
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Apply one op to a state held at `st` (shared or global memory), all
+// threads; each thread loads UNR groups before computing them, so a CTA that
+// sweeps a large state in global memory keeps enough loads in flight.
+template <class Ar, int K>
+__device__ __forceinline__ void apply_op(typename Ar::raw_t* st, int n, const BOp& op,
+                                         const typename Ar::coef_t* M, const uint64_t* moff) {
+  constexpr int D = 1 << K;
+  constexpr int UNR = D >= 8 ? 1 : 8 / D;
+  const uint64_t ngroups = 1ull << (n - op.nins);
+  for (uint64_t j0 = (uint64_t)threadIdx.x * UNR; j0 < ngroups; j0 += (uint64_t)kBT * UNR) {
+    uint64_t b[UNR];
+    typename Ar::val_t in[UNR][D];
+#pragma unroll
+    for (int u = 0; u < UNR; u++) {
+      const uint64_t j = j0 + u < ngroups ? j0 + u : j0;   // ngroups is a power of two >= UNR or 1
+      uint64_t x = j;
+      for (int i = 0; i < op.nins; i++) x = qc_insert_zero(x, op.ins[i]);
+      b[u] = x | op.orval;
+#pragma unroll
+      for (int r = 0; r < D; r++) in[u][r] = Ar::from_raw(st[b[u] + moff[r]]);
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; u++) {
+      if (u > 0 && j0 + u >= ngroups) break;
+#pragma unroll
+      for (int r = 0; r < D; r++) st[b[u] + moff[r]] = Ar::to_raw(Ar::template dot<D>(&M[r * D], in[u]));
+    }
+  }
+}
+
+template <class Ar>
+__global__ void __launch_bounds__(kBT, 2)
+k_batch(const BCirc* __restrict__ circs, const uint32_t* __restrict__ order, int ncirc,
+        const BOp* __restrict__ ops, const typename Ar::coef_t* __restrict__ coefs,
+        unsigned int* __restrict__ queue, unsigned long long* __restrict__ times) {
+  using raw_t = typename Ar::raw_t;
+  using coef_t = typename Ar::coef_t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  raw_t* sstate = reinterpret_cast<raw_t*>(smem);
+  coef_t* sM = reinterpret_cast<coef_t*>(smem + kSmemState);
+  uint64_t* smoff = reinterpret_cast<uint64_t*>(smem + kSmemState + kMaxD * kMaxD * sizeof(coef_t));
+  __shared__ unsigned int s_next;
+  if (threadIdx.x == 0) atomicMin(&times[ncirc], gtimer());   // launch start (earliest CTA)
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(queue, 1u);
+    __syncthreads();
+    const unsigned int qi = s_next;
+    __syncthreads();
+    if (qi >= (unsigned int)ncirc) break;
+    const uint32_t ci = order[qi];
+    const BCirc c = circs[ci];
+    const uint64_t N = 1ull << c.n;
+    raw_t* gst = reinterpret_cast<raw_t*>(c.state);
+    raw_t* st = c.smem ? sstate : gst;
+    raw_t zero;
+    zero.x = 0; zero.y = 0;
+    for (uint64_t i = threadIdx.x; i < N; i += kBT) st[i] = zero;
+    __syncthreads();
+    if (threadIdx.x == 0) { raw_t one; one.x = 1; one.y = 0; st[0] = one; }
+    for (uint32_t o = 0; o < c.nops; o++) {
+      const BOp op = ops[c.op0 + o];
+      const int D = 1 << op.k;
+      __syncthreads();   // previous op done (and its matrix no longer read)
+      for (int i = threadIdx.x; i < D * D; i += kBT) sM[i] = coefs[op.coef + i];
+      if (threadIdx.x < D) {
+        uint64_t off = 0;
+        for (int t = 0; t < op.k; t++)
+          if ((threadIdx.x >> (op.k - 1 - t)) & 1) off += 1ull << op.tpos[t];
+        smoff[threadIdx.x] = off;
+      }
+      __syncthreads();
+      switch (op.k) {
+        case 1: apply_op<Ar, 1>(st, c.n, op, sM, smoff); break;
+        case 2: apply_op<Ar, 2>(st, c.n, op, sM, smoff); break;
+        case 3: apply_op<Ar, 3>(st, c.n, op, sM, smoff); break;
+        default: apply_op<Ar, 4>(st, c.n, op, sM, smoff); break;
+      }
+    }
+    __syncthreads();
+    if (c.smem)
+      for (uint64_t i = threadIdx.x; i < N; i += kBT) gst[i] = sstate[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      times[ci] = gtimer();
+    }
+  }
+}
+
+}  // namespace
+
+struct qc_batch {
+  int ncirc = 0;
+  int dtype = QC_C64, arith = QC_ARITH_AUTO, device = 0;
+  int fuse_k = 0, nops = 0, nsmem = 0;
+  cudaStream_t stream = nullptr;
+  void* dmem = nullptr;        // [circs][order][ops][coefs][queue][times]
+  BCirc* dcircs = nullptr;
+  uint32_t* dorder = nullptr;
+  BOp* dops = nullptr;
+  void* dcoefs = nullptr;
+  unsigned int* dqueue = nullptr;
+  unsigned long long* dtimes = nullptr;
+  int grid = 1;
+  size_t smem = 0;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned long long> htimes;
+};
+
+namespace {
+
+template <class Ar>
+int build_tables(qc_batch* b, qc_state* const* states, const qc_circuit_desc* circs, int ncirc, int fuse_k) {
+  using coef_t = typename Ar::coef_t;
+  std::vector<BCirc> hc(ncirc);
+  std::vector<BOp> hops;
+  std::vector<coef_t> hcoef;
+  std::vector<double> work(ncirc);
+  b->nsmem = 0;
+  for (int i = 0; i < ncirc; i++) {
+    const qc_circuit_desc& d = circs[i];
+    std::vector<qc_op> ops;
+    if (int rc = qc_plan_ops(d.n, d.gates, d.ngates, fuse_k, ops)) return qc_fail(rc, "circuit %d: %s", i, qc_last_error());
+    hc[i].state = (uint64_t)(uintptr_t)states[i]->ptr;
+    hc[i].n = d.n;
+    hc[i].op0 = (uint32_t)hops.size();
+    hc[i].nops = (uint32_t)ops.size();
+    hc[i].smem = ((size_t)1 << d.n) * sizeof(typename Ar::raw_t) <= kSmemState ? 1 : 0;
+    b->nsmem += hc[i].smem;
+    for (const qc_op& op : ops) {
+      if (op.k > kMaxK) return qc_fail(QC_ERR_UNSUPPORTED, "circuit %d: gate on %d targets (batch path: <= %d)", i, op.k, kMaxK);
+      BOp bo;
+      std::memset(&bo, 0, sizeof(bo));
+      bo.coef = (uint32_t)hcoef.size();
+      bo.k = (uint8_t)op.k;
+      int ins[QC_MAX_INS], ni = 0;
+      for (int t = 0; t < op.k; t++) { bo.tpos[t] = (uint8_t)op.tpos[t]; ins[ni++] = op.tpos[t]; }
+      for (int t = 0; t < op.nc; t++) { ins[ni++] = op.cpos[t]; if (op.cval[t]) bo.orval |= 1ull << op.cpos[t]; }
+      std::sort(ins, ins + ni);
+      bo.nins = (uint8_t)ni;
+      for (int t = 0; t < ni; t++) bo.ins[t] = (uint8_t)ins[t];
+      const int D = 1 << op.k;
+      for (int e = 0; e < D * D; e++) hcoef.push_back(Ar::make_coef(op.U[2 * e], op.U[2 * e + 1]));
+      hops.push_back(bo);
+    }
+    // work estimate: sweeps over the state; shared-memory circuits cost a few times less per op
+    work[i] = (double)((size_t)1 << d.n) * (double)(ops.size() + 1) * (hc[i].smem ? 0.25 : 1.0);
+  }
+  std::vector<uint32_t> order(ncirc);
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) { return work[a] > work[c]; });
+  const size_t sz_c = sizeof(BCirc) * ncirc, sz_o = (sizeof(uint32_t) * ncirc + 15) & ~(size_t)15;
+  const size_t sz_op = sizeof(BOp) * std::max<size_t>(1, hops.size());
+  const size_t sz_cf = (sizeof(coef_t) * std::max<size_t>(1, hcoef.size()) + 15) & ~(size_t)15;
+  const size_t sz_t = sizeof(unsigned long long) * (ncirc + 1);
+  const size_t total = sz_c + sz_o + sz_op + sz_cf + 16 + sz_t;
+  void* m = nullptr;
+  cudaError_t e = cudaMalloc(&m, total);
+  if (e != cudaSuccess) { cudaGetLastError(); return qc_fail(QC_ERR_OOM, "batch tables (%zu bytes)", total); }
+  if (b->dmem) cudaFree(b->dmem);
+  b->dmem = m;
+  char* p = (char*)m;
+  b->dcircs = (BCirc*)p; p += sz_c;
+  b->dorder = (uint32_t*)p; p += sz_o;
+  b->dops = (BOp*)p; p += sz_op;
+  b->dcoefs = p; p += sz_cf;
+  b->dqueue = (unsigned int*)p; p += 16;
+  b->dtimes = (unsigned long long*)p;
+  QC_CUDA(cudaMemcpy(b->dcircs, hc.data(), sz_c, cudaMemcpyHostToDevice));
+  QC_CUDA(cudaMemcpy(b->dorder, order.data(), sizeof(uint32_t) * ncirc, cudaMemcpyHostToDevice));
+  if (!hops.empty()) QC_CUDA(cudaMemcpy(b->dops, hops.data(), sizeof(BOp) * hops.size(), cudaMemcpyHostToDevice));
+  if (!hcoef.empty()) QC_CUDA(cudaMemcpy(b->dcoefs, hcoef.data(), sizeof(coef_t) * hcoef.size(), cudaMemcpyHostToDevice));
+  b->nops = (int)hops.size();
+  b->fuse_k = fuse_k;
+  b->smem = kSmemState + kMaxD * kMaxD * sizeof(coef_t) + kMaxD * sizeof(uint64_t);
+  QC_CUDA(cudaFuncSetAttribute(k_batch<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  int per_sm = 0;
+  QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<Ar>, kBT, b->smem));
+  b->grid = std::max(1, std::min(ncirc, qc_num_sms() * std::max(1, per_sm)));
+  return QC_OK;
+}
+
+template <class Ar>
+int enqueue(qc_batch* b) {
+  QC_CUDA(cudaMemsetAsync(b->dqueue, 0, sizeof(unsigned int), b->stream));
+  QC_CUDA(cudaMemsetAsync(b->dtimes + b->ncirc, 0xFF, sizeof(unsigned long long), b->stream));
+  k_batch<Ar><<<b->grid, kBT, b->smem, b->stream>>>(b->dcircs, b->dorder, b->ncirc, b->dops,
+                                                   (const typename Ar::coef_t*)b->dcoefs, b->dqueue, b->dtimes);
+  QC_LAUNCHED("k_batch");
+  return QC_OK;
+}
+
+int enqueue_any(qc_batch* b) {
+  if (b->dtype == QC_C64) return enqueue<ArC64>(b);
+  if (b->arith == QC_ARITH_NATIVE) return enqueue<ArC128>(b);
+  return enqueue<ArC128x>(b);
+}
+
+int build_any(qc_batch* b, qc_state* const* states, const qc_circuit_desc* circs, int ncirc, int fuse_k) {
+  if (b->dtype == QC_C64) return build_tables<ArC64>(b, states, circs, ncirc, fuse_k);
+  if (b->arith == QC_ARITH_NATIVE) return build_tables<ArC128>(b, states, circs, ncirc, fuse_k);
+  return build_tables<ArC128x>(b, states, circs, ncirc, fuse_k);
+}
+
+int timed_run(qc_batch* b, float* ms) {
+  cudaEvent_t e0, e1;
+  QC_CUDA(cudaEventCreate(&e0));
+  QC_CUDA(cudaEventCreate(&e1));
+  cudaEventRecord(e0, b->stream);
+  int rc = enqueue_any(b);
+  cudaEventRecord(e1, b->stream);
+  if (rc == QC_OK) {
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) rc = qc_cuda_fail(e, "batch run");
+    else cudaEventElapsedTime(ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int qc_batch_create(qc_state* const* states, const qc_circuit_desc* circs, int ncirc,
+                               const qc_batch_opts* opts, qc_batch** out) {
+  if (!out) return qc_fail(QC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (ncirc < 1 || !states || !circs) return qc_fail(QC_ERR_ARG, "empty or NULL batch");
+  qc_batch_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.fuse_k > kMaxK) return qc_fail(QC_ERR_ARG, "fuse_k=%d (batch path supports up to %d)", o.fuse_k, kMaxK);
+  for (int i = 0; i < ncirc; i++) {
+    if (int rc = qc_check_state(states[i])) return qc_fail(rc, "state %d: %s", i, qc_last_error());
+    if (states[i]->n != circs[i].n) return qc_fail(QC_ERR_ARG, "state %d has n=%d, circuit has n=%d", i, states[i]->n, circs[i].n);
+    if (states[i]->dtype != states[0]->dtype || states[i]->arith != states[0]->arith || states[i]->device != states[0]->device)
+      return qc_fail(QC_ERR_ARG, "state %d: all states of a batch need one dtype, arith and device", i);
+    if (circs[i].ngates < 0 || (circs[i].ngates > 0 && !circs[i].gates)) return qc_fail(QC_ERR_ARG, "circuit %d: invalid gate list", i);
+  }
+  qc_batch* b = new qc_batch;
+  b->ncirc = ncirc;
+  b->dtype = states[0]->dtype;
+  b->arith = states[0]->arith;
+  b->device = states[0]->device;
+  b->stream = (cudaStream_t)o.stream;
+  b->htimes.resize(ncirc + 1);
+  int rc = QC_OK;
+  if (o.fuse_k < 0) {
+    // autotune: time the whole batch once per candidate width, keep the fastest
+    float best = 1e30f;
+    int bestk = 1;
+    for (int k : {1, 2, 3, 4}) {
+      rc = build_any(b, states, circs, ncirc, k);
+      float ms = 0.f;
+      if (rc == QC_OK) rc = timed_run(b, &ms);
+      if (rc != QC_OK) break;
+      if (ms < best) { best = ms; bestk = k; }
+    }
+    if (rc == QC_OK) rc = build_any(b, states, circs, ncirc, bestk);
+  } else {
+    rc = build_any(b, states, circs, ncirc, o.fuse_k);
+  }
+  if (rc == QC_OK && o.use_graph) {
+    if (!b->stream) rc = qc_fail(QC_ERR_ARG, "graph capture needs a non-default stream");
+    cudaGraph_t g = nullptr;
+    if (rc == QC_OK) {
+      cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) rc = qc_cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    if (rc == QC_OK) {
+      int rc2 = enqueue_any(b);
+      cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+      if (rc2 != QC_OK) rc = rc2;
+      else if (e != cudaSuccess) rc = qc_cuda_fail(e, "cudaStreamEndCapture");
+    }
+    if (rc == QC_OK) {
+      cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+      if (e != cudaSuccess) rc = qc_cuda_fail(e, "cudaGraphInstantiate");
+    }
+    if (g) cudaGraphDestroy(g);
+  }
+  if (rc != QC_OK) {
+    qc_batch_free(b);
+    return rc;
+  }
+  *out = b;
+  return QC_OK;
+}
+
+extern "C" int qc_batch_launch(qc_batch* b, double* completion_ms, double* total_ms) {
+  if (!b) return qc_fail(QC_ERR_ARG, "batch is NULL");
+  QC_CUDA(cudaSetDevice(b->device));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (total_ms) {
+    QC_CUDA(cudaEventCreate(&e0));
+    QC_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, b->stream);
+  }
+  int rc = QC_OK;
+  if (b->gexec) {
+    cudaError_t e = cudaGraphLaunch(b->gexec, b->stream);
+    if (e != cudaSuccess) rc = qc_cuda_fail(e, "cudaGraphLaunch");
+  } else {
+    rc = enqueue_any(b);
+  }
+  if (total_ms) cudaEventRecord(e1, b->stream);
+  if (rc == QC_OK && (completion_ms || total_ms)) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) rc = qc_cuda_fail(e, "batch run");
+    if (rc == QC_OK && completion_ms) {
+      e = cudaMemcpy(b->htimes.data(), b->dtimes, sizeof(unsigned long long) * (b->ncirc + 1), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) rc = qc_cuda_fail(e, "cudaMemcpy(times)");
+      const unsigned long long t0 = b->htimes[b->ncirc];
+      for (int i = 0; i < b->ncirc && rc == QC_OK; i++) completion_ms[i] = (double)(b->htimes[i] - t0) * 1e-6;
+    }
+    if (rc == QC_OK && total_ms) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      *total_ms = ms;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return rc;
+}
+
+extern "C" int qc_batch_info(const qc_batch* b, int* fuse_k, int* nops, int* nsmem) {
+  if (!b) return qc_fail(QC_ERR_ARG, "batch is NULL");
+  if (fuse_k) *fuse_k = b->fuse_k;
+  if (nops) *nops = b->nops;
+  if (nsmem) *nsmem = b->nsmem;
+  return QC_OK;
+}
+
+extern "C" int qc_batch_free(qc_batch* b) {
+  if (!b) return QC_OK;
+  cudaSetDevice(b->device);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->dmem) cudaFree(b->dmem);
+  delete b;
+  return QC_OK;
+}

@@ -247,7 +247,15 @@ int qc_gate_to_op(int n, const qc_gate& g, qc_op& op) {
 }
 
 namespace {
-// Build the launch plan (shared by qc_apply_circuit and qc_fuse_plan).
+int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops);
+}
+
+int qc_plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops) {
+  return plan_ops(n, gates, ngates, fuse_k, ops);
+}
+
+namespace {
+// Build the launch plan (shared by qc_apply_circuit, qc_fuse_plan and the batch path).
 int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops) {
   if (ngates < 0 || (ngates > 0 && !gates)) return qc_fail(QC_ERR_ARG, "invalid gate list");
   if (fuse_k < 0 || fuse_k > QC_MAX_TARGETS) return qc_fail(QC_ERR_ARG, "fuse_k=%d out of range 0..5", fuse_k);

@@ -291,6 +291,10 @@ struct qc_op {
 // qubits, builds the matrix (host FP64) and converts qubits to bit positions.
 int qc_gate_to_op(int n, const qc_gate& g, qc_op& op);
 
+// Launch plan of a circuit: one op per gate, or per fused block (fuse_k >= 2).
+#include <vector>
+int qc_plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops);
+
 // Apply one (controlled) k-qubit gate given by its matrix; the launcher
 // classifies the matrix (dense / permutation / diagonal) and picks a kernel.
 int qc_launch_op(qc_state* s, const qc_op& op);

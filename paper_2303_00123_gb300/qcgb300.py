@@ -48,6 +48,14 @@ class qc_block(ctypes.Structure):
                 ("U", ctypes.c_double * (2 * 32 * 32))]
 
 
+class qc_circuit_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("ngates", ctypes.c_int), ("gates", ctypes.POINTER(qc_gate))]
+
+
+class qc_batch_opts(ctypes.Structure):
+    _fields_ = [("fuse_k", ctypes.c_int), ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
 class qc_grad_opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("arith", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
@@ -88,6 +96,11 @@ def _load():
         "qc_adjoint_grad": [I, ctypes.POINTER(qc_gate), I, DP, I, ctypes.POINTER(qc_pauli_sum), DP, DP,
                             ctypes.POINTER(qc_grad_opts)],
         "qc_count_params": [ctypes.POINTER(qc_gate), I, IP],
+        "qc_batch_create": [ctypes.POINTER(P), ctypes.POINTER(qc_circuit_desc), I, ctypes.POINTER(qc_batch_opts),
+                            ctypes.POINTER(P)],
+        "qc_batch_launch": [P, DP, DP],
+        "qc_batch_info": [P, IP, IP, IP],
+        "qc_batch_free": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -342,6 +355,57 @@ def adjoint_grad(n: int, gates, hamiltonian, thetas=None, dtype: int = C128, ari
                                ctypes.byref(rec), _dptr(e), _dptr(g), ctypes.byref(o)))
     del keep, hk
     return e, g[:, :P]
+
+
+class Batch:
+    """Many independent circuits in one persistent launch (qc_batch_*).
+    `states[i]` receives circuits[i] applied to |0...0> at every launch()."""
+
+    def __init__(self, states, circuits, fuse_k: int = -1, use_graph: bool = False, stream=None):
+        if len(states) != len(circuits) or not states:
+            raise QCError(QC_ERR_ARG, "states and circuits must be non-empty and of equal length")
+        self.states = list(states)
+        self._keep = []
+        descs = (qc_circuit_desc * len(circuits))()
+        for i, (st, gates) in enumerate(zip(states, circuits)):
+            arr, keep = gate_records(gates)
+            self._keep.append((arr, keep))
+            descs[i].n = st.n
+            descs[i].ngates = len(gates)
+            descs[i].gates = arr
+        hs = (ctypes.c_void_p * len(states))(*[st.handle.value for st in states])
+        raw = getattr(stream, "cuda_stream", stream)
+        o = qc_batch_opts(int(fuse_k), int(bool(use_graph)), ctypes.c_void_p(raw or 0))
+        h = ctypes.c_void_p()
+        _check(lib.qc_batch_create(hs, descs, len(states), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._keep = None   # gate records are only read during qc_batch_create
+
+    def launch(self, timing: bool = False):
+        """Run; with timing=True returns (completion_ms per circuit, total_ms)."""
+        if not timing:
+            _check(lib.qc_batch_launch(self._h, None, None))
+            return None
+        comp = np.zeros(len(self.states), dtype=np.float64)
+        tot = ctypes.c_double(0.0)
+        _check(lib.qc_batch_launch(self._h, _dptr(comp), ctypes.byref(tot)))
+        return comp, tot.value
+
+    def info(self):
+        k, nops, nsm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.qc_batch_info(self._h, ctypes.byref(k), ctypes.byref(nops), ctypes.byref(nsm)))
+        return {"fuse_k": k.value, "ops": nops.value, "smem_circuits": nsm.value}
+
+    def free(self):
+        if getattr(self, "_h", None) is not None:
+            lib.qc_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def version() -> str:
