@@ -260,6 +260,73 @@ k_kq(char* __restrict__ st, const __grid_constant__ GeomK g, const __grid_consta
   }
 }
 
+// ---------------------------------------------------------------- fused tiles
+// Dense k-qubit block (k = 3..5, fused gates) over tiles of TG consecutive
+// groups.  With the TG groups taken along the lowest free bit positions, the
+// tile's amplitudes are 2^kh contiguous runs of L amplitudes (every position
+// below log2 L is a varying free bit or a target, or a low control); runs are
+// moved between HBM and shared memory with 32-byte vector accesses, the
+// matrix is applied in shared memory (inputs of a group go to registers,
+// outputs overwrite them in place), and the runs are written back.
+constexpr int kThreadsF = 256;
+
+struct GeomF {
+  uint64_t ntiles;            // tiles
+  uint64_t orval;             // control values (all positions)
+  uint64_t hoff[32];          // start offset of run h (high-target bits)
+  uint32_t loff[32];          // member r: in-run offset (low targets, low controls)
+  uint32_t run_of[32];        // member r: run index
+  uint32_t goff[128];         // group g: in-run offset (free low positions)
+  int nins;
+  int ins[QC_MAX_INS];
+  int tg_log;                 // log2 TG
+  int lb;                     // log2 L (run length in amplitudes)
+  int kh;                     // number of runs = 2^kh
+};
+
+template <class Ar, int K>
+__global__ void __launch_bounds__(kThreadsF)
+k_fused(vec32* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatD<Ar, (1 << K)> M) {
+  constexpr int D = 1 << K;
+  using raw_t = typename Ar::raw_t;
+  using val_t = typename Ar::val_t;
+  extern __shared__ __align__(32) unsigned char smem_f[];
+  raw_t* tile = reinterpret_cast<raw_t*>(smem_f);
+  const int TG = 1 << g.tg_log;
+  const uint32_t L = 1u << g.lb;
+  const uint32_t run_vecs = (L * Ar::E) / 32;          // 32-byte vectors per run
+  const uint32_t tile_vecs = run_vecs << g.kh;
+  const int tpg = kThreadsF / TG;                      // threads per group
+  const int grp = threadIdx.x % TG;
+  const int rsel = threadIdx.x / TG;
+  for (uint64_t T = blockIdx.x; T < g.ntiles; T += gridDim.x) {
+    uint64_t base = T << g.tg_log;
+    for (int i = 0; i < g.nins; i++) base = qc_insert_zero(base, g.ins[i]);
+    base = (base | g.orval) & ~(uint64_t)(L - 1);     // start of run 0 (amplitude index)
+    const vec32* src = st + (base * Ar::E) / 32;
+    // load runs
+#pragma unroll 4
+    for (uint32_t v = threadIdx.x; v < tile_vecs; v += kThreadsF) {
+      const uint32_t h = v / run_vecs, w = v - h * run_vecs;
+      reinterpret_cast<vec32*>(tile)[v] = qc_ld32(src + (g.hoff[h] * Ar::E) / 32 + w);
+    }
+    __syncthreads();
+    val_t in[D];
+#pragma unroll
+    for (int r = 0; r < D; r++) in[r] = Ar::from_raw(tile[g.run_of[r] * L + g.goff[grp] + g.loff[r]]);
+    __syncthreads();
+    for (int r = rsel; r < D; r += tpg)
+      tile[g.run_of[r] * L + g.goff[grp] + g.loff[r]] = Ar::to_raw(Ar::template dot<D>(&M.m[r * D], in));
+    __syncthreads();
+#pragma unroll 4
+    for (uint32_t v = threadIdx.x; v < tile_vecs; v += kThreadsF) {
+      const uint32_t h = v / run_vecs, w = v - h * run_vecs;
+      qc_st32(const_cast<vec32*>(src) + (g.hoff[h] * Ar::E) / 32 + w, reinterpret_cast<vec32*>(tile)[v]);
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- host side
 inline int grid_for(uint64_t work, int threads) {
   const uint64_t want = (work + threads - 1) / threads;
@@ -440,6 +507,109 @@ int launch_kq(qc_state* s, const qc_op& op) {
   return qc_fail(QC_ERR_ARG, "k-qubit gate with k=%d (1..5 supported)", op.k);
 }
 
+
+// Tile geometry for k_fused; returns false when the op does not suit it
+// (fewer than 32 groups, or a tile above the shared-memory budget).
+bool fused_geom(const qc_state* s, const qc_op& op, int E, GeomF& g, size_t& smem) {
+  std::memset(&g, 0, sizeof(g));
+  const int n = s->n, k = op.k, D = 1 << k;
+  int ins[QC_MAX_INS], nins = 0;
+  uint64_t used = 0;
+  for (int i = 0; i < k; i++) { ins[nins++] = op.tpos[i]; used |= 1ull << op.tpos[i]; }
+  for (int i = 0; i < op.nc; i++) {
+    ins[nins++] = op.cpos[i];
+    used |= 1ull << op.cpos[i];
+    if (op.cval[i]) g.orval |= 1ull << op.cpos[i];
+  }
+  std::sort(ins, ins + nins);
+  const int free_bits = n - nins;
+  for (int tg_log = 7; tg_log >= 5; tg_log--) {
+    if (tg_log > free_bits) continue;
+    // the tg_log lowest free positions
+    int got = 0, top = -1;
+    for (int p = 0; p < n && got < tg_log; p++)
+      if (!((used >> p) & 1)) { got++; top = p; }
+    const int lb = top + 1;
+    int kh = 0;
+    for (int i = 0; i < k; i++) if (op.tpos[i] >= lb) kh++;
+    const size_t bytes = ((size_t)1 << lb) * E << kh;
+    if (((size_t)1 << lb) * E < 32 || bytes > 96 * 1024) continue;
+    g.tg_log = tg_log;
+    g.lb = lb;
+    g.kh = kh;
+    g.nins = nins;
+    for (int i = 0; i < nins; i++) g.ins[i] = ins[i];
+    g.ntiles = 1ull << (free_bits - tg_log);
+    const uint64_t lmask = (1ull << lb) - 1;
+    // free low positions -> group offsets
+    for (int gi = 0; gi < (1 << tg_log); gi++) {
+      uint64_t x = 0;
+      int bit = 0;
+      for (int p = 0; p < lb; p++)
+        if (!((used >> p) & 1)) { if ((gi >> bit) & 1) x |= 1ull << p; bit++; }
+      g.goff[gi] = (uint32_t)x;
+    }
+    // members: low part and run index (high targets, in target order)
+    int hi_idx[QC_MAX_TARGETS], nh = 0;
+    for (int i = 0; i < k; i++) if (op.tpos[i] >= lb) hi_idx[nh++] = i;
+    for (int r = 0; r < D; r++) {
+      uint64_t lo = g.orval & lmask;
+      uint32_t run = 0;
+      for (int i = 0; i < k; i++) {
+        const int bitv = (r >> (k - 1 - i)) & 1;
+        if (op.tpos[i] < lb) { if (bitv) lo |= 1ull << op.tpos[i]; }
+      }
+      for (int h = 0; h < nh; h++) {
+        const int bitv = (r >> (k - 1 - hi_idx[h])) & 1;
+        run |= (uint32_t)bitv << (nh - 1 - h);
+      }
+      g.loff[r] = (uint32_t)lo;
+      g.run_of[r] = run;
+    }
+    for (int h = 0; h < (1 << nh); h++) {
+      uint64_t off = 0;
+      for (int j = 0; j < nh; j++) if ((h >> (nh - 1 - j)) & 1) off += 1ull << op.tpos[hi_idx[j]];
+      g.hoff[h] = off;
+    }
+    smem = bytes;
+    return true;
+  }
+  return false;
+}
+
+template <class Ar, int K>
+int launch_fused_t(qc_state* s, const qc_op& op, const GeomF& g, size_t smem) {
+  constexpr int D = 1 << K;
+  MatD<Ar, D> M;
+  for (int i = 0; i < D * D; i++) M.m[i] = Ar::make_coef(op.U[2 * i], op.U[2 * i + 1]);
+  static bool attr_set = false;
+  if (!attr_set) {
+    QC_CUDA(cudaFuncSetAttribute(k_fused<Ar, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    attr_set = true;
+  }
+  const uint64_t cap = (uint64_t)qc_num_sms() * 8;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
+  k_fused<Ar, K><<<grid, kThreadsF, smem, s->stream>>>((vec32*)s->ptr, g, M);
+  QC_LAUNCHED("k_fused");
+  return QC_OK;
+}
+
+template <class Ar>
+int launch_fused(qc_state* s, const qc_op& op, bool* done) {
+  *done = false;
+  GeomF g;
+  size_t smem = 0;
+  if (op.k < 3 || !fused_geom(s, op, Ar::E, g, smem)) return QC_OK;
+  *done = true;
+  switch (op.k) {
+    case 3: return launch_fused_t<Ar, 3>(s, op, g, smem);
+    case 4: return launch_fused_t<Ar, 4>(s, op, g, smem);
+    case 5: return launch_fused_t<Ar, 5>(s, op, g, smem);
+  }
+  *done = false;
+  return QC_OK;
+}
+
 // Reorder a 2-qubit matrix so that its first target has the higher bit position.
 void order_two_qubit(qc_op& op) {
   if (op.k != 2 || op.tpos[0] > op.tpos[1]) return;
@@ -460,7 +630,11 @@ int dispatch(qc_state* s, qc_op op) {
   const int E = Ar::E;
   // Wide gates (k >= 3) and states smaller than one 32-byte vector use k_kq.
   const bool tiny = s->n < L;
-  if (op.k >= 3) return launch_kq<Ar>(s, op);
+  if (op.k >= 3) {
+    bool done = false;
+    if (int rc = launch_fused<Ar>(s, op, &done)) return rc;
+    return done ? QC_OK : launch_kq<Ar>(s, op);
+  }
   order_two_qubit(op);
   const double* U = op.U;
   const int D = 1 << op.k;

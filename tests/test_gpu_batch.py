@@ -77,8 +77,8 @@ def test_batch_graph_replay_and_wide_controls(q):
 
 def test_batch_rejects_mismatched_states(q):
     sts = make_states(q, [5, 6], "c64")
-    with pytest.raises(q.QCError):
-        q.Batch(sts, [C.random_mix(5, 3, seed=1), C.random_mix(7, 3, seed=2)])
+    with pytest.raises(q.QCError):   # a gate on qubit 6 of a 6-qubit state
+        q.Batch(sts, [C.random_mix(5, 3, seed=1), [C.Gate("H", (6,))]])
     st128 = q.State(6, q.C128)
     with pytest.raises(q.QCError):
         q.Batch([sts[0], st128], [C.random_mix(5, 3, seed=1), C.random_mix(6, 3, seed=2)])

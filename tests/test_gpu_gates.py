@@ -398,3 +398,28 @@ def test_fused_brickwork_n30_c64_matches_unfused_on_samples(q):
         ref *= g.matrix[bit, 0]
     assert maxerr(got, ref) <= 2e-5
     st.free()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_fused_tile_kernel_placements(q, mode):
+    """Dense k-qubit blocks (k = 3, 4, 5) through the tile kernel: targets at
+    low, high and mixed bit positions, in any order, with and without low and
+    high controls, n = 14 and 17 (many tiles; ragged placements)."""
+    rng = np.random.default_rng(321)
+    for n in (14, 17):
+        phi = C.random_state(n, 400 + n)
+        st = new_state(q, n, mode)
+        cases = [[n - 1, n - 2, n - 3], [0, 1, 2, 3], [n - 1, 0, n // 2, 3, n - 4], [5, 9, 2],
+                 [n - 6, n - 5, n - 7, n - 1]]
+        for qs in cases:
+            for ctl in ([], [n // 3], [n - 1 if n - 1 not in qs else 4], [6, 7]):
+                if set(ctl) & set(qs):
+                    continue
+                cst = [int(v) for v in rng.integers(0, 2, size=len(ctl))]
+                U = rand_u(rng, 1 << len(qs))
+                st.from_numpy(phi)
+                st.apply_kq(U, qs, ctl, cst)
+                ref = phi.copy()
+                O.apply_matrix(ref, n, U, qs, ctl, cst)
+                assert maxerr(st.to_numpy().astype(np.complex128), ref) <= TOL[mode], (n, qs, ctl)
+        st.free()
