@@ -291,6 +291,12 @@ def case_gates(kind, n, rng):
             gates.append(C.Gate("SWAP", (t, (t + n // 2) % n)))
         elif kind == "h":
             gates.append(C.Gate("H", (t,)))
+        elif kind.startswith("kq"):
+            k = int(kind[2:])
+            qs = [(t + 3 * i) % n for i in range(k)]
+            if len(set(qs)) < k:
+                continue
+            gates.append(C.Gate("UK", tuple(qs), matrix=C.haar_unitary(rng, 1 << k)))
         else:
             raise SystemExit("unknown case " + kind)
     return gates
@@ -379,6 +385,64 @@ def run_batch_case(args):
                       "speedup": round(base_tot / tot, 2), "autotune_s": round(tune_s, 2)}))
 
 
+def run_fused_case(args):
+    """Brickwork depth 40 at n qubits with greedy fusion k = 0 (gate by gate),
+    2, 3, 4, 5: time, launches, gates/s, and effective HBM GB/s (sum of the
+    launches' algorithmic bytes 2*N*E / time); amplitude error against the
+    FP64 oracle on the same circuit family at n_err qubits."""
+    import torch
+    from paper_2303_00123_gb300 import qcgb300 as q
+    n = args.n
+    dt = q.C64 if args.dtype == "c64" else q.C128
+    elem = 8 if dt == q.C64 else 16
+    gates = C.brickwork(n, BRICK_DEPTH, seed=SEED_BRICK)
+    t = torch.empty(1 << n, dtype=torch.complex64 if dt == q.C64 else torch.complex128, device="cuda")
+    st = q.State.from_tensor(t)
+    st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
+    st.set_fused_tc(not args.no_tc)
+    stream = torch.cuda.Stream()
+    st.set_stream(stream)
+    res = {}
+    for k in (0, 2, 3, 4, 5):
+        for _ in range(args.warmup):
+            st.set_basis(0)
+            st.apply_circuit(gates, fuse_k=k)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st.set_basis(0)
+            nl, _ = st.apply_circuit(gates, fuse_k=k)
+        ev1.record(stream)
+        stream.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        res[str(k)] = {"ms": round(ms, 2), "launches": nl, "gates_per_s": round(len(gates) / ms * 1e3, 1),
+                       "eff_GBps": round(nl * 2 * (1 << n) * elem / (ms * 1e-3) / 1e9, 1)}
+    st.free()
+    del t
+    torch.cuda.empty_cache()
+    # accuracy against the oracle at n_err
+    err = {}
+    if args.n_err > 0:
+        from oracle import oracle as O
+        ne = args.n_err
+        g2 = C.brickwork(ne, BRICK_DEPTH, seed=SEED_BRICK)
+        ref = O.run_circuit(ne, g2)
+        for k in (0, 2, 3, 4, 5):
+            s2 = q.State(ne, dt)
+            s2.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
+            s2.set_fused_tc(not args.no_tc)
+            s2.apply_circuit(g2, fuse_k=k)
+            got = s2.to_numpy().astype(np.complex128)
+            s2.free()
+            err[str(k)] = {"max_abs": float(np.max(np.abs(got - ref))),
+                           "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+    print(json.dumps({"case": "fused", "n": n, "dtype": args.dtype, "arith": args.arith, "gates": len(gates),
+                      "tensor_cores": (not args.no_tc) and args.dtype == "c64",
+                      "by_fuse_k": res, "n_err": args.n_err, "error_vs_oracle": err,
+                      "speedup_best_vs_unfused": round(res["0"]["ms"] / min(v["ms"] for v in res.values()), 2)}))
+
+
 def run_case(args):
     """Per-target-qubit timing of one gate kind on an n-qubit state."""
     import torch
@@ -387,12 +451,15 @@ def run_case(args):
         return run_adjoint_case(args)
     if args.case == "batch":
         return run_batch_case(args)
+    if args.case == "fused":
+        return run_fused_case(args)
     n = args.n
     dt = q.C64 if args.dtype == "c64" else q.C128
     elem = 8 if dt == q.C64 else 16
     t = torch.zeros(1 << n, dtype=torch.complex64 if dt == q.C64 else torch.complex128, device="cuda")
     st = q.State.from_tensor(t)
     st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
+    st.set_fused_tc(not args.no_tc)
     stream = torch.cuda.Stream()
     st.set_stream(stream)
     st.set_basis(0)
@@ -407,11 +474,11 @@ def run_case(args):
     out = []
     for g, m in zip(gates, per):
         b = algorithmic_bytes(g, n, elem)
-        out.append({"q": g.qubits[0], "stride": 1 << (n - 1 - g.qubits[0]), "ms": round(float(m), 4),
+        out.append({"q": g.qubits[0], "qubits": list(g.qubits), "stride": 1 << (n - 1 - g.qubits[0]), "ms": round(float(m), 4),
                     "GBps": round(b / (m * 1e-3) / 1e9, 1)})
     peak, _ = measured_peaks()
     tot_b = sum(algorithmic_bytes(g, n, elem) for g in gates)
-    print(json.dumps({"case": args.case, "n": n, "dtype": args.dtype, "arith": args.arith,
+    print(json.dumps({"case": args.case, "n": n, "dtype": args.dtype, "arith": args.arith, "tc": not args.no_tc,
                       "avg_GBps": round(tot_b / (per.sum() * 1e-3) / 1e9, 1),
                       "frac_of_measured_hbm": round(tot_b / (per.sum() * 1e-3) / 1e9 / peak, 4),
                       "per_target": out}))
@@ -462,6 +529,8 @@ def main():
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--n-err", dest="n_err", type=int, default=0)
+    ap.add_argument("--no-tc", dest="no_tc", action="store_true", help="complex64 blocks on CUDA cores")
     args = ap.parse_args()
     if args.case:
         run_case(args)

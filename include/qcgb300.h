@@ -104,6 +104,17 @@ int qc_set_stream(qc_state* s, void* cuda_stream);
 /* Select the arithmetic for complex128 gate sweeps (qc_arith). */
 int qc_set_arith(qc_state* s, int arith);
 
+/* complex64 dense blocks on k >= 3 qubits (fused gates, qc_apply_kq) run on
+ * the tensor cores (tcgen05, split-TF32: hi*hi + hi*lo + lo*hi in FP32) when
+ * enable != 0 (the default), else on the CUDA cores in FP32. */
+int qc_set_fused_tc(qc_state* s, int enable);
+
+/* Device-side health counters: *tc_timeouts = number of tensor-core tile
+ * waits that hit their iteration limit since the library was loaded (each
+ * such wait sets the counter, abandons its tile and frees its tensor memory;
+ * 0 in normal operation).  Synchronises the device. */
+int qc_device_status(int* tc_timeouts);
+
 /* ---- single gates --------------------------------------------------------
  * qc_apply_1q: Sec. 2.1, Alg. 1.  U[8] = 2x2 complex row-major
  * (u00, u01, u10, u11), each as (re, im).  For every pair of basis indices

@@ -20,6 +20,7 @@ struct qc_state {
   int owned;            // 1: allocated by qc_state_alloc
   int arith;            // qc_arith for QC_C128
   int device;           // CUDA device ordinal the memory lives on
+  int fused_tc;         // 1: complex64 k-qubit blocks (k >= 3) on the tensor cores
   cudaStream_t stream;  // work queue
 };
 
@@ -290,6 +291,9 @@ struct qc_op {
 // Resolve a gate record (named or explicit matrix) into an op: validates the
 // qubits, builds the matrix (host FP64) and converts qubits to bit positions.
 int qc_gate_to_op(int n, const qc_gate& g, qc_op& op);
+
+// Number of tensor-core tile waits that gave up (device counter; 0 normally).
+int qc_tc_timeouts(int* count);
 
 // Launch plan of a circuit: one op per gate, or per fused block (fuse_k >= 2).
 #include <vector>

@@ -327,6 +327,198 @@ k_fused(vec32* __restrict__ st, const __grid_constant__ GeomF g, const __grid_co
   }
 }
 
+// ---------------------------------------------------------------- fused tiles, tensor cores
+// complex64 dense k-qubit block (k = 3..5) on the 5th-generation tensor cores.
+// For the 128 groups of a tile, V (128 x 2D reals: Re x_0..x_{D-1}, Im ...)
+// times R^T, with R = [[Ur, -Ui], [Ui, Ur]] the real form of U, gives the
+// outputs (Re, Im) of every group: one M=128, N=K=2D GEMM per tile.  TF32 keeps
+// 11 significant bits, so operands are split into hi + lo TF32 parts and three
+// products (hi*hi + hi*lo + lo*hi) are accumulated in FP32 in tensor memory
+// (about 2^-22 relative error, the precision of the FP32 state itself).
+// Operands live in shared memory in the K-major, no-swizzle layout (8-row x
+// 16-byte core matrices; LBO = 128 B between core matrices along K, SBO =
+// (2D/4)*128 B between 8-row groups); one thread issues the tcgen05.mma
+// instructions and commits them to an mbarrier; every thread then reads its
+// own row of the accumulator with tcgen05.ld and stores it.  Thread g of the
+// CTA owns group g of the tile for loads, stores and its accumulator row; the
+// next tile's inputs are loaded before the current tile's MMAs are awaited.
+static __device__ int g_tc_timeouts = 0;   // bounded mbarrier waits that gave up
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version for tcgen05; base offset 0; no swizzle
+  return d;
+}
+
+// byte offset of element (row, col) in a K-major no-swizzle operand with KR columns
+__device__ __forceinline__ uint32_t kmaj_off(int row, int col, int KR) {
+  return (row >> 3) * (KR >> 2) * 128 + (col >> 2) * 128 + (row & 7) * 16 + (col & 3) * 4;
+}
+
+template <int K>
+struct MatC64 { float2 u[(1 << K) * (1 << K)]; };
+
+template <int K>
+__global__ void __launch_bounds__(128)
+k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC64<K> U) {
+  constexpr int D = 1 << K;
+  constexpr int KR = 2 * D;                       // GEMM N = K
+  constexpr uint32_t NCOL = KR < 32 ? 32 : KR;    // TMEM columns
+  constexpr uint32_t SBO = (KR / 4) * 128;
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* sAh = smem_tc;                   // 128 x KR tf32
+  unsigned char* sAl = sAh + 128 * KR * 4;
+  unsigned char* sBh = sAl + 128 * KR * 4;        // KR x KR tf32 (row n = output n)
+  unsigned char* sBl = sBh + KR * KR * 4;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ uint64_t s_moff[D];                  // element offset of member r within a group
+  const int t = threadIdx.x;                      // = group within the tile = accumulator row
+  const int w = t >> 5;
+  const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
+  // B = R^T in K-major form is R row by row: B[n][k] = R[n][k]
+  for (int i = t; i < KR * KR; i += 128) {
+    const int n = i / KR, k = i % KR;
+    const int rn = n % D, rk = k % D;
+    const float2 u = U.u[rn * D + rk];
+    float v;
+    if (n < D) v = k < D ? u.x : -u.y;
+    else v = k < D ? u.y : u.x;
+    const uint32_t hi = tf32_rna(v);
+    const uint32_t lo = tf32_rna(v - __uint_as_float(hi));
+    *reinterpret_cast<uint32_t*>(sBh + kmaj_off(n, k, KR)) = hi;
+    *reinterpret_cast<uint32_t*>(sBl + kmaj_off(n, k, KR)) = lo;
+  }
+  if (t < D) s_moff[t] = g.hoff[g.run_of[t]] + g.loff[t];
+  if (t == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar_a) : "memory");
+  if (w == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_slot);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(dst), "r"(NCOL) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  const uint32_t aH = (uint32_t)__cvta_generic_to_shared(sAh), aL = (uint32_t)__cvta_generic_to_shared(sAl);
+  const uint32_t bH = (uint32_t)__cvta_generic_to_shared(sBh), bL = (uint32_t)__cvta_generic_to_shared(sBl);
+  const uint32_t L = 1u << g.lb;
+  const uint64_t* moff = s_moff;
+  const uint64_t goff = g.goff[t];
+  auto tile_base = [&](uint64_t T) {
+    uint64_t b = T << g.tg_log;
+    for (int i = 0; i < g.nins; i++) b = qc_insert_zero(b, g.ins[i]);
+    return ((b | g.orval) & ~(uint64_t)(L - 1)) + goff;
+  };
+  float2 x[D];
+  uint64_t T = blockIdx.x;
+  uint64_t base = 0;
+  if (T < g.ntiles) {
+    base = tile_base(T);
+#pragma unroll
+    for (int r = 0; r < D; r++) x[r] = st[base + moff[r]];
+  }
+  uint32_t phase = 0;
+  bool ok = true;
+  for (; T < g.ntiles && ok; T += gridDim.x) {
+    // split this tile's inputs into the A operands (row t)
+#pragma unroll
+    for (int c4 = 0; c4 < KR / 4; c4++) {
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int col = c4 * 4 + j;
+        const float v = col < D ? x[col].x : x[col - D].y;
+        hi[j] = tf32_rna(v);
+        lo[j] = tf32_rna(v - __uint_as_float(hi[j]));
+      }
+      *reinterpret_cast<uint4*>(sAh + kmaj_off(t, c4 * 4, KR)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(sAl + kmaj_off(t, c4 * 4, KR)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (t == 0) {
+#pragma unroll
+      for (int p = 0; p < 3; p++) {
+        const uint32_t a = p == 2 ? aL : aH;
+        const uint32_t b = p == 1 ? bL : bH;
+#pragma unroll
+        for (int kk = 0; kk < KR / 8; kk++) {
+          const uint64_t ad = umma_desc(a + kk * 256, 128, SBO);
+          const uint64_t bd = umma_desc(b + kk * 256, 128, SBO);
+          const uint32_t acc = (p > 0 || kk > 0) ? 1u : 0u;
+          asm volatile("{ .reg .pred q; setp.ne.b32 q, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q; }"
+                       :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar_a) : "memory");
+    }
+    // prefetch the next tile while the tensor cores work
+    const uint64_t curbase = base;
+    const uint64_t Tn = T + gridDim.x;
+    if (Tn < g.ntiles) {
+      base = tile_base(Tn);
+#pragma unroll
+      for (int r = 0; r < D; r++) x[r] = st[base + moff[r]];
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; it++)
+      asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
+                   : "=r"(done) : "r"(mbar_a), "r"(phase) : "memory");
+    phase ^= 1u;
+    done = __syncthreads_and(done);   // one decision for the whole CTA (tcgen05.ld is warp-collective)
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!done) {
+      if (t == 0) atomicAdd(&g_tc_timeouts, 1);
+      ok = false;
+    } else {
+      // accumulator row t: columns 0..D-1 = Re of the outputs, D..2D-1 = Im
+      constexpr int CH = D < 16 ? D : 16;          // outputs per chunk pair
+#pragma unroll
+      for (int c = 0; c < D; c += CH) {
+        uint32_t re[16], im[16];
+        const uint32_t row = tmem + ((uint32_t)(32 * w) << 16);
+        if constexpr (CH == 16) {
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                       : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
+                         "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]), "=r"(re[14]), "=r"(re[15])
+                       : "r"(row + (uint32_t)c));
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                       : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7]),
+                         "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]), "=r"(im[14]), "=r"(im[15])
+                       : "r"(row + (uint32_t)(D + c)));
+        } else {   // D = 8: one 16-column load holds Re (0..7) and Im (8..15)
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                       : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
+                         "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7])
+                       : "r"(row));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < CH; j++)
+          st[curbase + moff[c + j]] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL) : "memory");
+}
+
 // ---------------------------------------------------------------- host side
 inline int grid_for(uint64_t work, int threads) {
   const uint64_t want = (work + threads - 1) / threads;
@@ -610,6 +802,42 @@ int launch_fused(qc_state* s, const qc_op& op, bool* done) {
   return QC_OK;
 }
 
+
+template <int K>
+int launch_fused_tc_t(qc_state* s, const qc_op& op, const GeomF& g) {
+  constexpr int D = 1 << K, KR = 2 * D;
+  MatC64<K> U;
+  for (int i = 0; i < D * D; i++) U.u[i] = make_float2((float)op.U[2 * i], (float)op.U[2 * i + 1]);
+  const size_t smem = (size_t)2 * 128 * KR * 4 + (size_t)2 * KR * KR * 4;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    QC_CUDA(cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tc<K>, 128, smem));
+    const int ncol = KR < 32 ? 32 : KR;
+    per_sm = std::max(1, std::min(per_sm, 512 / ncol));   // every resident CTA gets its TMEM columns
+  }
+  const uint64_t cap = (uint64_t)qc_num_sms() * per_sm;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
+  k_fused_tc<K><<<grid, 128, smem, s->stream>>>((float2*)s->ptr, g, U);
+  QC_LAUNCHED("k_fused_tc");
+  return QC_OK;
+}
+
+// complex64 k = 3..5 blocks with 128-group tiles go to the tensor cores.
+int launch_fused_tc(qc_state* s, const qc_op& op, bool* done) {
+  *done = false;
+  if (op.k < 3 || op.k > 5 || s->n - op.k - op.nc < 7) return QC_OK;
+  GeomF g;
+  size_t smem = 0;
+  if (!fused_geom(s, op, 8, g, smem) || g.tg_log != 7) return QC_OK;
+  *done = true;
+  switch (op.k) {
+    case 3: return launch_fused_tc_t<3>(s, op, g);
+    case 4: return launch_fused_tc_t<4>(s, op, g);
+    default: return launch_fused_tc_t<5>(s, op, g);
+  }
+}
+
 // Reorder a 2-qubit matrix so that its first target has the higher bit position.
 void order_two_qubit(qc_op& op) {
   if (op.k != 2 || op.tpos[0] > op.tpos[1]) return;
@@ -632,6 +860,12 @@ int dispatch(qc_state* s, qc_op op) {
   const bool tiny = s->n < L;
   if (op.k >= 3) {
     bool done = false;
+    if constexpr (Ar::V == 4) {
+      if (s->fused_tc) {
+        if (int rc = launch_fused_tc(s, op, &done)) return rc;
+        if (done) return QC_OK;
+      }
+    }
     if (int rc = launch_fused<Ar>(s, op, &done)) return rc;
     return done ? QC_OK : launch_kq<Ar>(s, op);
   }
@@ -672,6 +906,11 @@ int dispatch(qc_state* s, qc_op op) {
 }
 
 }  // namespace
+
+int qc_tc_timeouts(int* count) {
+  QC_CUDA(cudaMemcpyFromSymbol(count, g_tc_timeouts, sizeof(int)));
+  return QC_OK;
+}
 
 int qc_launch_op(qc_state* s, const qc_op& op) {
   if (s->dtype == QC_C64) return dispatch<ArC64>(s, op);

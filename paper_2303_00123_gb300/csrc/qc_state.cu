@@ -82,6 +82,7 @@ static int new_handle(void* ptr, int n, int dtype, int owned, qc_state** out) {
   s->dtype = dtype;
   s->owned = owned;
   s->arith = QC_ARITH_AUTO;
+  s->fused_tc = 1;
   s->stream = nullptr;
   cudaGetDevice(&s->device);
   *out = s;
@@ -181,6 +182,17 @@ int qc_set_stream(qc_state* s, void* stream) {
   if (!s) return qc_fail(QC_ERR_ARG, "state handle is NULL");
   s->stream = (cudaStream_t)stream;
   return QC_OK;
+}
+
+int qc_set_fused_tc(qc_state* s, int enable) {
+  if (!s) return qc_fail(QC_ERR_ARG, "state handle is NULL");
+  s->fused_tc = enable ? 1 : 0;
+  return QC_OK;
+}
+
+int qc_device_status(int* tc_timeouts) {
+  if (!tc_timeouts) return qc_fail(QC_ERR_ARG, "tc_timeouts is NULL");
+  return qc_tc_timeouts(tc_timeouts);
 }
 
 int qc_set_arith(qc_state* s, int arith) {

@@ -85,6 +85,8 @@ def _load():
         "qc_state_info": [P, ctypes.POINTER(P), IP, IP],
         "qc_set_stream": [P, P],
         "qc_set_arith": [P, I],
+        "qc_set_fused_tc": [P, I],
+        "qc_device_status": [IP],
         "qc_apply_1q": [P, DP, I],
         "qc_apply_c1q": [P, DP, IP, IP, I, I],
         "qc_apply_2q": [P, DP, I, I],
@@ -243,6 +245,10 @@ class State:
     def set_arith(self, arith: int):
         _check(lib.qc_set_arith(self._h, arith))
 
+    def set_fused_tc(self, enable: bool):
+        """complex64 k>=3 blocks on the tensor cores (default) or CUDA cores."""
+        _check(lib.qc_set_fused_tc(self._h, int(bool(enable))))
+
     def set_basis(self, x: int = 0):
         _check(lib.qc_state_set_basis(self._h, ctypes.c_uint64(x)))
 
@@ -323,6 +329,12 @@ def fuse_plan(n: int, gates, fuse_k: int):
         out.append((tuple(b.qubits[:b.k]), tuple(b.controls[:b.nc]), tuple(b.cstates[:b.nc]), U.copy()))
     del keep
     return out
+
+
+def device_status() -> dict:
+    t = ctypes.c_int(0)
+    _check(lib.qc_device_status(ctypes.byref(t)))
+    return {"tc_timeouts": t.value}
 
 
 def count_params(gates) -> int:

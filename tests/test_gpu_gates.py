@@ -423,3 +423,33 @@ def test_fused_tile_kernel_placements(q, mode):
                 O.apply_matrix(ref, n, U, qs, ctl, cst)
                 assert maxerr(st.to_numpy().astype(np.complex128), ref) <= TOL[mode], (n, qs, ctl)
         st.free()
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_tensor_core_blocks_match_oracle_and_cuda_cores(q, k):
+    """complex64 k-qubit blocks: the tcgen05 path (split TF32) and the FP32
+    CUDA-core path both within 2e-5 of the oracle; placements with low and
+    high targets, ragged controls; n = 12 (one tile per CTA) and 16."""
+    rng = np.random.default_rng(900 + k)
+    for n in (12, 16):
+        phi = C.random_state(n, 77 + n)
+        for trial in range(4):
+            qs = [int(v) for v in rng.choice(n, size=k, replace=False)]
+            rest = [x for x in range(n) if x not in qs]
+            ctl = [int(v) for v in rng.choice(rest, size=trial % 2, replace=False)]
+            cst = [1] * len(ctl)
+            U = rand_u(rng, 1 << k)
+            ref = phi.copy()
+            O.apply_matrix(ref, n, U, qs, ctl, cst)
+            outs = []
+            for tc in (True, False):
+                st = q.State(n, q.C64)
+                st.set_fused_tc(tc)
+                st.from_numpy(phi)
+                st.apply_kq(U, qs, ctl, cst)
+                outs.append(st.to_numpy().astype(np.complex128))
+                st.free()
+            for o in outs:
+                assert maxerr(o, ref) <= 2e-5, (n, qs, ctl)
+            assert maxerr(outs[0], outs[1]) <= 2e-5
+    assert q.device_status()["tc_timeouts"] == 0
