@@ -366,12 +366,33 @@ __device__ __forceinline__ uint32_t kmaj_off(int row, int col, int KR) {
 template <int K>
 struct MatC64 { float2 u[(1 << K) * (1 << K)]; };
 
+// tcgen05.ld of N consecutive 32-bit columns of this warp's lane block.
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t* r) {
+  if constexpr (N == 16) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(addr));
+  } else if constexpr (N == 8) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+  } else {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
+  }
+}
+
+constexpr int kThreadsTC = 256;   // two threads per accumulator row, each owns half of the members
+
 template <int K>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kThreadsTC, 2)
 k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC64<K> U) {
   constexpr int D = 1 << K;
+  constexpr int H = D / 2;                        // members per thread
   constexpr int KR = 2 * D;                       // GEMM N = K
-  constexpr uint32_t NCOL = KR < 32 ? 32 : KR;    // TMEM columns
+  constexpr uint32_t NCOL = 2 * KR < 32 ? 32 : 2 * KR;   // big + small accumulators
   constexpr uint32_t SBO = (KR / 4) * 128;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* sAh = smem_tc;                   // 128 x KR tf32
@@ -381,17 +402,16 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ uint64_t s_moff[D];                  // element offset of member r within a group
-  const int t = threadIdx.x;                      // = group within the tile = accumulator row
+  const int t = threadIdx.x;
   const int w = t >> 5;
+  const int row = t & 127;                        // group within the tile = accumulator row (lane)
+  const int m0 = (t >> 7) * H;                    // first member of this thread
   const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
-  // B = R^T in K-major form is R row by row: B[n][k] = R[n][k]
-  for (int i = t; i < KR * KR; i += 128) {
+  // B = R^T in K-major form is R row by row: B[n][k] = R[n][k], R = [[Ur, -Ui], [Ui, Ur]]
+  for (int i = t; i < KR * KR; i += kThreadsTC) {
     const int n = i / KR, k = i % KR;
-    const int rn = n % D, rk = k % D;
-    const float2 u = U.u[rn * D + rk];
-    float v;
-    if (n < D) v = k < D ? u.x : -u.y;
-    else v = k < D ? u.y : u.x;
+    const float2 u = U.u[(n % D) * D + (k % D)];
+    const float v = n < D ? (k < D ? u.x : -u.y) : (k < D ? u.y : u.x);
     const uint32_t hi = tf32_rna(v);
     const uint32_t lo = tf32_rna(v - __uint_as_float(hi));
     *reinterpret_cast<uint32_t*>(sBh + kmaj_off(n, k, KR)) = hi;
@@ -409,58 +429,65 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   const uint32_t aH = (uint32_t)__cvta_generic_to_shared(sAh), aL = (uint32_t)__cvta_generic_to_shared(sAl);
   const uint32_t bH = (uint32_t)__cvta_generic_to_shared(sBh), bL = (uint32_t)__cvta_generic_to_shared(sBl);
   const uint32_t L = 1u << g.lb;
-  const uint64_t* moff = s_moff;
-  const uint64_t goff = g.goff[t];
+  const uint64_t* moff = s_moff + m0;             // shared-memory table (broadcast reads)
+  const uint64_t goff = g.goff[row];
   auto tile_base = [&](uint64_t T) {
     uint64_t b = T << g.tg_log;
     for (int i = 0; i < g.nins; i++) b = qc_insert_zero(b, g.ins[i]);
     return ((b | g.orval) & ~(uint64_t)(L - 1)) + goff;
   };
-  float2 x[D];
+  float2 x[H];
   uint64_t T = blockIdx.x;
   uint64_t base = 0;
   if (T < g.ntiles) {
     base = tile_base(T);
 #pragma unroll
-    for (int r = 0; r < D; r++) x[r] = st[base + moff[r]];
+    for (int r = 0; r < H; r++) x[r] = st[base + moff[r]];
   }
   uint32_t phase = 0;
   bool ok = true;
   for (; T < g.ntiles && ok; T += gridDim.x) {
-    // split this tile's inputs into the A operands (row t)
+    // split this thread's members into the A operands: Re -> column m0+r, Im -> column D+m0+r
 #pragma unroll
-    for (int c4 = 0; c4 < KR / 4; c4++) {
-      uint32_t hi[4], lo[4];
+    for (int part = 0; part < 2; part++) {
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const int col = c4 * 4 + j;
-        const float v = col < D ? x[col].x : x[col - D].y;
-        hi[j] = tf32_rna(v);
-        lo[j] = tf32_rna(v - __uint_as_float(hi[j]));
+      for (int c4 = 0; c4 < H; c4 += 4) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const float v = part == 0 ? x[c4 + j].x : x[c4 + j].y;
+          hi[j] = tf32_rna(v);
+          lo[j] = tf32_rna(v - __uint_as_float(hi[j]));
+        }
+        const int col = part * D + m0 + c4;
+        *reinterpret_cast<uint4*>(sAh + kmaj_off(row, col, KR)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(sAl + kmaj_off(row, col, KR)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
       }
-      *reinterpret_cast<uint4*>(sAh + kmaj_off(t, c4 * 4, KR)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      *reinterpret_cast<uint4*>(sAl + kmaj_off(t, c4 * 4, KR)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (t == 0) {
+      // columns [0, KR): hi*hi; columns [KR, 2KR): hi*lo + lo*hi.  Keeping the
+      // small products in their own accumulator stops the tensor core's FP32
+      // accumulation from dropping their low bits against the large sum.
 #pragma unroll
       for (int p = 0; p < 3; p++) {
         const uint32_t a = p == 2 ? aL : aH;
         const uint32_t b = p == 1 ? bL : bH;
+        const uint32_t d = p == 0 ? tmem : tmem + (uint32_t)KR;
 #pragma unroll
         for (int kk = 0; kk < KR / 8; kk++) {
           const uint64_t ad = umma_desc(a + kk * 256, 128, SBO);
           const uint64_t bd = umma_desc(b + kk * 256, 128, SBO);
-          const uint32_t acc = (p > 0 || kk > 0) ? 1u : 0u;
+          const uint32_t acc = (p == 2 || kk > 0) ? 1u : 0u;
           asm volatile("{ .reg .pred q; setp.ne.b32 q, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q; }"
-                       :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                       :: "r"(d), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar_a) : "memory");
@@ -471,7 +498,7 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
     if (Tn < g.ntiles) {
       base = tile_base(Tn);
 #pragma unroll
-      for (int r = 0; r < D; r++) x[r] = st[base + moff[r]];
+      for (int r = 0; r < H; r++) x[r] = st[base + moff[r]];
     }
     uint32_t done = 0;
     for (int it = 0; it < (1 << 24) && !done; it++)
@@ -484,31 +511,21 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
       if (t == 0) atomicAdd(&g_tc_timeouts, 1);
       ok = false;
     } else {
-      // accumulator row t: columns 0..D-1 = Re of the outputs, D..2D-1 = Im
-      constexpr int CH = D < 16 ? D : 16;          // outputs per chunk pair
+      // accumulator row: columns m0..m0+H-1 = Re, D+m0.. = Im of this thread's outputs
+      const uint32_t lane = tmem + ((uint32_t)(32 * (w & 3)) << 16);
+      constexpr int NC = H < 16 ? H : 16;
 #pragma unroll
-      for (int c = 0; c < D; c += CH) {
-        uint32_t re[16], im[16];
-        const uint32_t row = tmem + ((uint32_t)(32 * w) << 16);
-        if constexpr (CH == 16) {
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                       : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
-                         "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]), "=r"(re[14]), "=r"(re[15])
-                       : "r"(row + (uint32_t)c));
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                       : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7]),
-                         "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]), "=r"(im[14]), "=r"(im[15])
-                       : "r"(row + (uint32_t)(D + c)));
-        } else {   // D = 8: one 16-column load holds Re (0..7) and Im (8..15)
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                       : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
-                         "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7])
-                       : "r"(row));
-        }
+      for (int c = 0; c < H; c += NC) {
+        uint32_t re0[NC], im0[NC], re1[NC], im1[NC];
+        tmem_ld<NC>(lane + (uint32_t)(m0 + c), re0);
+        tmem_ld<NC>(lane + (uint32_t)(D + m0 + c), im0);
+        tmem_ld<NC>(lane + (uint32_t)(KR + m0 + c), re1);
+        tmem_ld<NC>(lane + (uint32_t)(KR + D + m0 + c), im1);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < CH; j++)
-          st[curbase + moff[c + j]] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+        for (int j = 0; j < NC; j++)
+          st[curbase + moff[c + j]] = make_float2(__uint_as_float(re0[j]) + __uint_as_float(re1[j]),
+                                                  __uint_as_float(im0[j]) + __uint_as_float(im1[j]));
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -812,13 +829,13 @@ int launch_fused_tc_t(qc_state* s, const qc_op& op, const GeomF& g) {
   static int per_sm = 0;
   if (per_sm == 0) {
     QC_CUDA(cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tc<K>, 128, smem));
-    const int ncol = KR < 32 ? 32 : KR;
+    QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tc<K>, kThreadsTC, smem));
+    const int ncol = 2 * KR < 32 ? 32 : 2 * KR;
     per_sm = std::max(1, std::min(per_sm, 512 / ncol));   // every resident CTA gets its TMEM columns
   }
   const uint64_t cap = (uint64_t)qc_num_sms() * per_sm;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
-  k_fused_tc<K><<<grid, 128, smem, s->stream>>>((float2*)s->ptr, g, U);
+  k_fused_tc<K><<<grid, kThreadsTC, smem, s->stream>>>((float2*)s->ptr, g, U);
   QC_LAUNCHED("k_fused_tc");
   return QC_OK;
 }
