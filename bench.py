@@ -252,6 +252,7 @@ def run_gpu(args):
         e2e = {"value": gates_per_step * args.steps * world / e2e_s, "unit": "gates/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi}
 
+    extras = {} if args.no_extras else extra_measurements(q, st, stream, brick, x)
     line = {
         "metric": "gates/s at n=30 complex128 (QFT 480 + brickwork depth-40 1780 gates, unfused)",
         "value": round(value, 3), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -266,6 +267,7 @@ def run_gpu(args):
         "e2e": e2e,
         "clocks": clk.summary(),
     }
+    line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample()
     st.free()
@@ -485,6 +487,102 @@ def run_case(args):
     st.free()
 
 
+def _event_ms(stream, fn, reps=1):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    stream.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_measurements(q, st, stream, brick, x):
+    """Fused, batched and adjoint forms against the plain per-gate form, on
+    this GPU, outside the main timed region (each reported with its config)."""
+    import torch
+    out = {}
+    # fused brickwork (n=30): complex128 (float-float, k=2 blocks) and complex64 (tensor cores, k=5)
+    fused = {}
+    def brick_run(state, k):
+        state.set_basis(0)
+        state.apply_circuit(brick, fuse_k=k)
+    brick_run(st, 2)
+    t0 = _event_ms(stream, lambda: brick_run(st, 0))
+    t2 = _event_ms(stream, lambda: brick_run(st, 2))
+    fused["c128_k2"] = {"ms": round(t2, 1), "unfused_ms": round(t0, 1), "speedup": round(t0 / t2, 2),
+                        "launches": len(q.fuse_plan(N_QUBITS, brick, 2))}
+    t64 = torch.empty(1 << N_QUBITS, dtype=torch.complex64, device="cuda")
+    s64 = q.State.from_tensor(t64)
+    s64.set_stream(stream)
+    brick_run(s64, 5)
+    u0 = _event_ms(stream, lambda: brick_run(s64, 0))
+    u5 = _event_ms(stream, lambda: brick_run(s64, 5))
+    fused["c64_k5_tensor_cores"] = {"ms": round(u5, 1), "unfused_ms": round(u0, 1), "speedup": round(u0 / u5, 2),
+                                    "launches": len(q.fuse_plan(N_QUBITS, brick, 5))}
+    s64.free()
+    del t64
+    torch.cuda.empty_cache()
+    out["fused"] = {"workload": "brickwork depth 40, n=30, greedy fusion", **fused}
+    # batched: 1024 circuits, one persistent launch vs one launch per gate
+    specs = C.batch_specs(1024, seed=4)
+    circs = [C.random_mix(n, d, seed=sd) for n, d, sd in specs]
+    ngates = sum(len(g) for g in circs)
+    sts = [q.State(n, q.C64) for n, _, _ in specs]
+    b = q.Batch(sts, circs, fuse_k=-1, use_graph=True, stream=stream)
+    b.launch(timing=True)
+    comp, tot = b.launch(timing=True)
+    info = b.info()
+    b.free()
+    for s2 in sts:
+        s2.set_stream(stream)
+    def one_by_one():
+        for s2, g in zip(sts, circs):
+            s2.set_basis(0)
+            s2.apply_circuit(g)
+    one_by_one()
+    tb = _event_ms(stream, one_by_one)
+    for s2 in sts:
+        s2.free()
+    out["batched"] = {"workload": "1024 random circuits, n~U[10,24], depth~U[50,300], complex64",
+                      "gates": ngates, "persistent_ms": round(tot, 1), "gates_per_s": round(ngates / tot * 1e3, 1),
+                      "p50_ms": round(float(np.percentile(comp, 50)), 1), "p99_ms": round(float(np.percentile(comp, 99)), 1),
+                      "one_launch_per_gate_ms": round(tb, 1), "speedup": round(tb / tot, 2), "fuse_k": info["fuse_k"]}
+    # adjoint gradients vs parameter shift through the per-gate path (sampled, extrapolated)
+    n, layers, B = 20, 10, 64
+    th = C.hea_thetas(n, layers, seed=2025, batch=B)
+    H = C.tfim(n, 1.0)
+    gates = C.hea(n, layers, th[0])
+    q.adjoint_grad(n, gates, H, th, dtype=q.C64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        q.adjoint_grad(n, gates, H, th, dtype=q.C64)
+    ta = (time.perf_counter() - t0) / 2
+    sp = q.State(n, q.C64)
+    sp.set_stream(stream)
+    def energy_eval():
+        sp.set_basis(0)
+        sp.apply_circuit(gates)
+        return sp.expect(H)
+    energy_eval()
+    t0 = time.perf_counter()
+    for _ in range(8):
+        energy_eval()
+    te = (time.perf_counter() - t0) / 8
+    sp.free()
+    nparam = 2 * n * layers
+    ps_per_set = 2 * nparam * te
+    out["adjoint"] = {"workload": "HEA n=20, 10 layers, 400 parameters, TFIM, batch 64, complex64 sweeps + FP64 reductions",
+                      "s_per_batch": round(ta, 4), "gradient_sets_per_s": round(B / ta, 1),
+                      "param_shift_s_per_set_extrapolated": round(ps_per_set, 3),
+                      "speedup_vs_param_shift": round(ps_per_set / (ta / B), 1),
+                      "note": "parameter shift timed as 8 energy evaluations (circuit + expectation) and scaled to 800"}
+    return out
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -525,6 +623,8 @@ def main():
     ap.add_argument("--fuse", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", dest="no_extras", action="store_true",
+                    help="skip the fused / batched / adjoint side measurements")
     ap.add_argument("--case", default=None, help="micro-benchmark: dense1q, dense2q, cnot, cphase, swap, h")
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
