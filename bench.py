@@ -41,6 +41,20 @@ SEED_BRICK = 1001
 HBM_FALLBACK = 6800.0
 
 
+def aggregate_ranks(elapsed_s: float, units_per_rank: float, dist=None, device="cpu"):
+    """Replicas: every rank processes `units_per_rank`; the job's time is the
+    slowest rank's.  Returns (max elapsed over ranks, total units / that time)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_s = float(t.item())
+        dist.barrier()
+    return elapsed_s, units_per_rank * world / elapsed_s
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -210,13 +224,7 @@ def run_gpu(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    if dist:
-        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
-        dist.barrier()
-    total_gates = gates_per_step * args.steps * world
-    value = total_gates / elapsed
+    elapsed, value = aggregate_ranks(elapsed, gates_per_step * args.steps, dist, "cuda")
 
     peak, peak_kind = measured_peaks()
     roof = None
@@ -462,6 +470,7 @@ def run_case(args):
     st = q.State.from_tensor(t)
     st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
     st.set_fused_tc(not args.no_tc)
+    st.set_packed(not args.no_packed)
     stream = torch.cuda.Stream()
     st.set_stream(stream)
     st.set_basis(0)
@@ -481,6 +490,7 @@ def run_case(args):
     peak, _ = measured_peaks()
     tot_b = sum(algorithmic_bytes(g, n, elem) for g in gates)
     print(json.dumps({"case": args.case, "n": n, "dtype": args.dtype, "arith": args.arith, "tc": not args.no_tc,
+                      "packed": not args.no_packed,
                       "avg_GBps": round(tot_b / (per.sum() * 1e-3) / 1e9, 1),
                       "frac_of_measured_hbm": round(tot_b / (per.sum() * 1e-3) / 1e9 / peak, 4),
                       "per_target": out}))
@@ -631,6 +641,7 @@ def main():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--n-err", dest="n_err", type=int, default=0)
     ap.add_argument("--no-tc", dest="no_tc", action="store_true", help="complex64 blocks on CUDA cores")
+    ap.add_argument("--no-packed", dest="no_packed", action="store_true", help="scalar FP32 float-float")
     args = ap.parse_args()
     if args.case:
         run_case(args)

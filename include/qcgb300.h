@@ -109,6 +109,12 @@ int qc_set_arith(qc_state* s, int arith);
  * enable != 0 (the default), else on the CUDA cores in FP32. */
 int qc_set_fused_tc(qc_state* s, int enable);
 
+/* complex128 float-float dense and phase sweeps use packed FP32-pair
+ * instructions (add/mul/fma .f32x2, two FP32 operations per issue slot; the
+ * default, enable != 0) or scalar FP32 instructions.  Both perform the same
+ * operations in the same order, so results are identical. */
+int qc_set_packed(qc_state* s, int enable);
+
 /* Device-side health counters: *tc_timeouts = number of tensor-core tile
  * waits that hit their iteration limit since the library was loaded (each
  * such wait sets the counter, abandons its tile and frees its tensor memory;
@@ -212,8 +218,10 @@ int qc_fuse_plan(int n, const qc_gate* gates, int ngates, int fuse_k,
  * Each CTA takes circuits from an atomic work queue, largest first; a circuit
  * whose state fits in the CTA's shared memory (complex64 n <= 13, complex128
  * n <= 12) is simulated there from |0...0> and written to its state once;
- * larger ones are swept in global memory by the CTA, gate block by gate block.
- * CTAs never wait on one another.  Fusion (greedy, k <= 4) is applied per
+ * larger ones are swept in global memory by a team of up to 16 CTAs (one per
+ * 8 MB of state), which split every gate block and meet at a bounded barrier
+ * between blocks; a barrier that gives up makes qc_batch_launch return
+ * QC_ERR_TIMEOUT (results incomplete).  Fusion (greedy, k <= 4) is applied per
  * circuit; fuse_k < 0 lets the library time the candidates {1, 2, 3, 4} on the
  * batch once and keep the fastest. */
 typedef struct {
@@ -226,6 +234,9 @@ typedef struct {
   int fuse_k;     /* -1: autotune; 0 or 1: gate by gate; 2..4: fusion width */
   int use_graph;  /* 1: capture the launch in a CUDA graph, replayed by qc_batch_launch */
   void* stream;   /* cudaStream_t or NULL */
+  long long spin_limit;   /* team-barrier wait limit in polls (0: default 2^26, ~10 s) */
+  int test_skip_circuit;  /* testing only: 1 + index of a circuit whose member ... */
+  int test_skip_member;   /* ... never arrives at its team barriers (0 = off) */
 } qc_batch_opts;
 
 typedef struct qc_batch qc_batch;

@@ -5,14 +5,22 @@
 // and per-circuit records go to one device allocation.  Circuits are ordered by
 // work (2^n * ops), largest first.
 //
-// Device: a persistent kernel with as many CTAs as fit at once.  A CTA takes
-// the next circuit from an atomic queue and runs all of it:
-//   * shared-memory mode (state <= kSmemState bytes): the state is built as
-//     |0...0> in shared memory, every op is applied there (threads over the
-//     op's groups, __syncthreads between ops), and the final state is written
-//     to HBM once -- one pass over HBM for the whole circuit;
-//   * global mode: the state is initialised in place and swept op by op.
-// CTAs never wait on other CTAs (no inter-CTA barrier, no spin loop).
+// Device: a persistent kernel with as many CTAs as fit at once (all of them
+// co-resident).  A CTA takes the next entry from an atomic queue:
+//   * shared-memory mode (state <= kSmemState bytes): one CTA builds the state
+//     as |0...0> in shared memory, applies every op there (threads over the
+//     op's groups, __syncthreads between ops) and writes the final state to
+//     HBM once -- one pass over HBM for the whole circuit;
+//   * global mode: a team of T CTAs (T = 1..16 by state size; the circuit has
+//     T consecutive queue entries) initialises the state in place and sweeps it
+//     op by op, each member taking 1/T of every op's groups, with a team
+//     barrier (a per-circuit arrival counter) between ops.
+// Deadlock freedom: the grid never exceeds the co-resident capacity, team
+// entries are consecutive and T <= 16 < grid, so at most one team is partly
+// dequeued at any time and its missing members are the next entries taken by
+// CTAs that finish work that waits on nothing unfinished.  Every barrier wait
+// is bounded; a wait that gives up sets a status word (the host returns
+// QC_ERR_TIMEOUT) and the team abandons that circuit.
 // %globaltimer stamps give each circuit's completion time.
 #include <algorithm>
 #include <cstring>
@@ -42,6 +50,20 @@ struct BCirc {
   uint32_t op0, nops; // op range
   int n;
   int smem;           // 1: shared-memory mode
+  int team;           // CTAs working on this circuit (1 in shared-memory mode)
+};
+
+struct BEntry {
+  uint32_t circ;      // circuit index
+  uint32_t member;    // 0..team-1
+};
+
+struct BCtl {
+  unsigned int queue;       // next entry
+  int status;               // 0, or 1 when a team barrier gave up
+  int skip_circ;            // test hook: this circuit's member `skip_member` never arrives (-1: off)
+  int skip_member;
+  unsigned long long spin_limit;
 };
 
 __device__ __forceinline__ uint64_t gtimer() {
@@ -53,38 +75,68 @@ __device__ __forceinline__ uint64_t gtimer() {
 // Apply one op to a state held at `st` (shared or global memory), all
 // threads; each thread loads UNR groups before computing them, so a CTA that
 // sweeps a large state in global memory keeps enough loads in flight.
-template <class Ar, int K>
-__device__ __forceinline__ void apply_op(typename Ar::raw_t* st, int n, const BOp& op,
-                                         const typename Ar::coef_t* M, const uint64_t* moff) {
+// State reads: shared memory, or global memory through L2 only (ld.global.cg):
+// team members on other SMs write the state between ops, and L1 is not
+// coherent across SMs, so a cached line could be stale after a team barrier.
+template <bool GLOBAL, class T>
+__device__ __forceinline__ T ld_state(const T* p) {
+  if constexpr (GLOBAL) return __ldcg(p);
+  else return *p;
+}
+
+template <class Ar, int K, bool GLOBAL>
+__device__ __forceinline__ void apply_op(typename Ar::raw_t* st, const BOp& op, const typename Ar::coef_t* M,
+                                         const uint64_t* moff, uint64_t g0, uint64_t g1) {
   constexpr int D = 1 << K;
   constexpr int UNR = D >= 8 ? 1 : 8 / D;
-  const uint64_t ngroups = 1ull << (n - op.nins);
-  for (uint64_t j0 = (uint64_t)threadIdx.x * UNR; j0 < ngroups; j0 += (uint64_t)kBT * UNR) {
+  for (uint64_t j0 = g0 + (uint64_t)threadIdx.x * UNR; j0 < g1; j0 += (uint64_t)kBT * UNR) {
     uint64_t b[UNR];
     typename Ar::val_t in[UNR][D];
 #pragma unroll
     for (int u = 0; u < UNR; u++) {
-      const uint64_t j = j0 + u < ngroups ? j0 + u : j0;   // ngroups is a power of two >= UNR or 1
+      const uint64_t j = j0 + u < g1 ? j0 + u : j0;   // duplicates of j0 are read, never written
       uint64_t x = j;
       for (int i = 0; i < op.nins; i++) x = qc_insert_zero(x, op.ins[i]);
       b[u] = x | op.orval;
 #pragma unroll
-      for (int r = 0; r < D; r++) in[u][r] = Ar::from_raw(st[b[u] + moff[r]]);
+      for (int r = 0; r < D; r++) in[u][r] = Ar::from_raw(ld_state<GLOBAL>(st + b[u] + moff[r]));
     }
 #pragma unroll
     for (int u = 0; u < UNR; u++) {
-      if (u > 0 && j0 + u >= ngroups) break;
+      if (u > 0 && j0 + u >= g1) break;
 #pragma unroll
       for (int r = 0; r < D; r++) st[b[u] + moff[r]] = Ar::to_raw(Ar::template dot<D>(&M[r * D], in[u]));
     }
   }
 }
 
+// Team barrier: every member arrives once per phase; returns false when the
+// bounded wait gave up (the status word is then set).
+__device__ bool team_barrier(unsigned int* bar, unsigned int target, bool arrive, BCtl* ctl) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (arrive) atomicAdd(bar, 1u);
+    int ok = 1;
+    unsigned long long it = 0;
+    while (atomicAdd(bar, 0u) < target) {
+      if (++it > ctl->spin_limit || atomicAdd(&ctl->status, 0) != 0) { ok = 0; break; }
+      __nanosleep(128);
+    }
+    if (!ok) atomicExch(&ctl->status, 1);
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 template <class Ar>
 __global__ void __launch_bounds__(kBT, 2)
-k_batch(const BCirc* __restrict__ circs, const uint32_t* __restrict__ order, int ncirc,
+k_batch(const BCirc* __restrict__ circs, const BEntry* __restrict__ entries, int nentries, int ncirc,
         const BOp* __restrict__ ops, const typename Ar::coef_t* __restrict__ coefs,
-        unsigned int* __restrict__ queue, unsigned long long* __restrict__ times) {
+        BCtl* __restrict__ ctl, unsigned int* __restrict__ bars, unsigned long long* __restrict__ times) {
   using raw_t = typename Ar::raw_t;
   using coef_t = typename Ar::coef_t;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -94,22 +146,29 @@ k_batch(const BCirc* __restrict__ circs, const uint32_t* __restrict__ order, int
   __shared__ unsigned int s_next;
   if (threadIdx.x == 0) atomicMin(&times[ncirc], gtimer());   // launch start (earliest CTA)
   for (;;) {
-    if (threadIdx.x == 0) s_next = atomicAdd(queue, 1u);
+    if (threadIdx.x == 0) s_next = atomicAdd(&ctl->queue, 1u);
     __syncthreads();
     const unsigned int qi = s_next;
     __syncthreads();
-    if (qi >= (unsigned int)ncirc) break;
-    const uint32_t ci = order[qi];
-    const BCirc c = circs[ci];
+    if (qi >= (unsigned int)nentries) break;
+    const BEntry e = entries[qi];
+    const BCirc c = circs[e.circ];
     const uint64_t N = 1ull << c.n;
     raw_t* gst = reinterpret_cast<raw_t*>(c.state);
     raw_t* st = c.smem ? sstate : gst;
+    const uint32_t T = (uint32_t)c.team, m = e.member;
+    const bool arrive = !(ctl->skip_circ == (int)e.circ && ctl->skip_member == (int)m);
+    unsigned int* bar = bars + e.circ;
     raw_t zero;
     zero.x = 0; zero.y = 0;
-    for (uint64_t i = threadIdx.x; i < N; i += kBT) st[i] = zero;
+    {
+      const uint64_t a0 = N / T * m, a1 = N / T * (m + 1);
+      for (uint64_t i = a0 + threadIdx.x; i < a1; i += kBT) st[i] = zero;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) { raw_t one; one.x = 1; one.y = 0; st[0] = one; }
-    for (uint32_t o = 0; o < c.nops; o++) {
+    if (threadIdx.x == 0 && m == 0) { raw_t one; one.x = 1; one.y = 0; st[0] = one; }
+    bool ok = T == 1 ? true : team_barrier(bar, T, arrive, ctl);
+    for (uint32_t o = 0; o < c.nops && ok; o++) {
       const BOp op = ops[c.op0 + o];
       const int D = 1 << op.k;
       __syncthreads();   // previous op done (and its matrix no longer read)
@@ -121,20 +180,32 @@ k_batch(const BCirc* __restrict__ circs, const uint32_t* __restrict__ order, int
         smoff[threadIdx.x] = off;
       }
       __syncthreads();
-      switch (op.k) {
-        case 1: apply_op<Ar, 1>(st, c.n, op, sM, smoff); break;
-        case 2: apply_op<Ar, 2>(st, c.n, op, sM, smoff); break;
-        case 3: apply_op<Ar, 3>(st, c.n, op, sM, smoff); break;
-        default: apply_op<Ar, 4>(st, c.n, op, sM, smoff); break;
+      const uint64_t G = 1ull << (c.n - op.nins);
+      const uint64_t g0 = G * m / T, g1 = G * (m + 1) / T;
+      if (c.smem) {
+        switch (op.k) {
+          case 1: apply_op<Ar, 1, false>(st, op, sM, smoff, g0, g1); break;
+          case 2: apply_op<Ar, 2, false>(st, op, sM, smoff, g0, g1); break;
+          case 3: apply_op<Ar, 3, false>(st, op, sM, smoff, g0, g1); break;
+          default: apply_op<Ar, 4, false>(st, op, sM, smoff, g0, g1); break;
+        }
+      } else {
+        switch (op.k) {
+          case 1: apply_op<Ar, 1, true>(st, op, sM, smoff, g0, g1); break;
+          case 2: apply_op<Ar, 2, true>(st, op, sM, smoff, g0, g1); break;
+          case 3: apply_op<Ar, 3, true>(st, op, sM, smoff, g0, g1); break;
+          default: apply_op<Ar, 4, true>(st, op, sM, smoff, g0, g1); break;
+        }
       }
+      if (T > 1) ok = team_barrier(bar, T * (o + 2), arrive, ctl);
     }
     __syncthreads();
     if (c.smem)
       for (uint64_t i = threadIdx.x; i < N; i += kBT) gst[i] = sstate[i];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && m == 0) {
       __threadfence();
-      times[ci] = gtimer();
+      times[e.circ] = gtimer();
     }
   }
 }
@@ -146,13 +217,16 @@ struct qc_batch {
   int dtype = QC_C64, arith = QC_ARITH_AUTO, device = 0;
   int fuse_k = 0, nops = 0, nsmem = 0;
   cudaStream_t stream = nullptr;
-  void* dmem = nullptr;        // [circs][order][ops][coefs][queue][times]
+  void* dmem = nullptr;        // [circs][entries][ops][coefs][ctl][bars][times]
   BCirc* dcircs = nullptr;
-  uint32_t* dorder = nullptr;
+  BEntry* dentries = nullptr;
+  int nentries = 0;
   BOp* dops = nullptr;
   void* dcoefs = nullptr;
-  unsigned int* dqueue = nullptr;
+  BCtl* dctl = nullptr;
+  unsigned int* dbars = nullptr;
   unsigned long long* dtimes = nullptr;
+  BCtl hctl;
   int grid = 1;
   size_t smem = 0;
   cudaGraphExec_t gexec = nullptr;
@@ -195,17 +269,32 @@ int build_tables(qc_batch* b, qc_state* const* states, const qc_circuit_desc* ci
       for (int e = 0; e < D * D; e++) hcoef.push_back(Ar::make_coef(op.U[2 * e], op.U[2 * e + 1]));
       hops.push_back(bo);
     }
-    // work estimate: sweeps over the state; shared-memory circuits cost a few times less per op
-    work[i] = (double)((size_t)1 << d.n) * (double)(ops.size() + 1) * (hc[i].smem ? 0.25 : 1.0);
+    // team size: one CTA per 8 MB of state beyond shared memory, at most 16
+    if (hc[i].smem) {
+      hc[i].team = 1;
+    } else {
+      const size_t bytes = ((size_t)1 << d.n) * sizeof(typename Ar::raw_t);
+      int T = 1;
+      while (T < 16 && bytes / (size_t)T > ((size_t)8 << 20)) T *= 2;
+      hc[i].team = T;
+    }
+    // work per member: sweeps over the state; shared-memory circuits cost a few times less per op
+    work[i] = (double)((size_t)1 << d.n) * (double)(ops.size() + 1) * (hc[i].smem ? 0.25 : 1.0) / hc[i].team;
   }
+  // queue: largest work per member first; a team's entries are consecutive
   std::vector<uint32_t> order(ncirc);
   std::iota(order.begin(), order.end(), 0u);
   std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) { return work[a] > work[c]; });
-  const size_t sz_c = sizeof(BCirc) * ncirc, sz_o = (sizeof(uint32_t) * ncirc + 15) & ~(size_t)15;
+  std::vector<BEntry> ents;
+  for (uint32_t ci : order)
+    for (int m = 0; m < hc[ci].team; m++) ents.push_back(BEntry{ci, (uint32_t)m});
+  const size_t sz_c = sizeof(BCirc) * ncirc, sz_e = (sizeof(BEntry) * ents.size() + 15) & ~(size_t)15;
   const size_t sz_op = sizeof(BOp) * std::max<size_t>(1, hops.size());
   const size_t sz_cf = (sizeof(coef_t) * std::max<size_t>(1, hcoef.size()) + 15) & ~(size_t)15;
+  const size_t sz_ctl = (sizeof(BCtl) + 15) & ~(size_t)15;
+  const size_t sz_b = (sizeof(unsigned int) * ncirc + 15) & ~(size_t)15;
   const size_t sz_t = sizeof(unsigned long long) * (ncirc + 1);
-  const size_t total = sz_c + sz_o + sz_op + sz_cf + 16 + sz_t;
+  const size_t total = sz_c + sz_e + sz_op + sz_cf + sz_ctl + sz_b + sz_t;
   void* m = nullptr;
   cudaError_t e = cudaMalloc(&m, total);
   if (e != cudaSuccess) { cudaGetLastError(); return qc_fail(QC_ERR_OOM, "batch tables (%zu bytes)", total); }
@@ -213,32 +302,47 @@ int build_tables(qc_batch* b, qc_state* const* states, const qc_circuit_desc* ci
   b->dmem = m;
   char* p = (char*)m;
   b->dcircs = (BCirc*)p; p += sz_c;
-  b->dorder = (uint32_t*)p; p += sz_o;
+  b->dentries = (BEntry*)p; p += sz_e;
   b->dops = (BOp*)p; p += sz_op;
   b->dcoefs = p; p += sz_cf;
-  b->dqueue = (unsigned int*)p; p += 16;
+  b->dctl = (BCtl*)p; p += sz_ctl;
+  b->dbars = (unsigned int*)p; p += sz_b;
   b->dtimes = (unsigned long long*)p;
+  b->nentries = (int)ents.size();
   QC_CUDA(cudaMemcpy(b->dcircs, hc.data(), sz_c, cudaMemcpyHostToDevice));
-  QC_CUDA(cudaMemcpy(b->dorder, order.data(), sizeof(uint32_t) * ncirc, cudaMemcpyHostToDevice));
+  QC_CUDA(cudaMemcpy(b->dentries, ents.data(), sizeof(BEntry) * ents.size(), cudaMemcpyHostToDevice));
   if (!hops.empty()) QC_CUDA(cudaMemcpy(b->dops, hops.data(), sizeof(BOp) * hops.size(), cudaMemcpyHostToDevice));
   if (!hcoef.empty()) QC_CUDA(cudaMemcpy(b->dcoefs, hcoef.data(), sizeof(coef_t) * hcoef.size(), cudaMemcpyHostToDevice));
   b->nops = (int)hops.size();
   b->fuse_k = fuse_k;
   b->smem = kSmemState + kMaxD * kMaxD * sizeof(coef_t) + kMaxD * sizeof(uint64_t);
   QC_CUDA(cudaFuncSetAttribute(k_batch<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  QC_CUDA(cudaFuncSetAttribute(k_batch<Ar>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared));
   int per_sm = 0;
   QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<Ar>, kBT, b->smem));
-  b->grid = std::max(1, std::min(ncirc, qc_num_sms() * std::max(1, per_sm)));
+  // never more CTAs than can be resident at once: team barriers rely on it
+  b->grid = std::max(1, std::min(b->nentries, qc_num_sms() * std::max(1, per_sm)));
+  if (b->grid < 16 && b->nentries > b->grid) return qc_fail(QC_ERR_UNSUPPORTED, "device too small for batch teams");
   return QC_OK;
 }
 
 template <class Ar>
 int enqueue(qc_batch* b) {
-  QC_CUDA(cudaMemsetAsync(b->dqueue, 0, sizeof(unsigned int), b->stream));
+  QC_CUDA(cudaMemcpyAsync(b->dctl, &b->hctl, sizeof(BCtl), cudaMemcpyHostToDevice, b->stream));
+  QC_CUDA(cudaMemsetAsync(b->dbars, 0, sizeof(unsigned int) * b->ncirc, b->stream));
   QC_CUDA(cudaMemsetAsync(b->dtimes + b->ncirc, 0xFF, sizeof(unsigned long long), b->stream));
-  k_batch<Ar><<<b->grid, kBT, b->smem, b->stream>>>(b->dcircs, b->dorder, b->ncirc, b->dops,
-                                                   (const typename Ar::coef_t*)b->dcoefs, b->dqueue, b->dtimes);
+  k_batch<Ar><<<b->grid, kBT, b->smem, b->stream>>>(b->dcircs, b->dentries, b->nentries, b->ncirc, b->dops,
+                                                   (const typename Ar::coef_t*)b->dcoefs, b->dctl, b->dbars,
+                                                   b->dtimes);
   QC_LAUNCHED("k_batch");
+  return QC_OK;
+}
+
+int read_status(qc_batch* b) {
+  int st = 0;
+  QC_CUDA(cudaMemcpy(&st, &b->dctl->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) return qc_fail(QC_ERR_TIMEOUT, "a team barrier of the batch kernel gave up; results are incomplete");
   return QC_OK;
 }
 
@@ -266,6 +370,7 @@ int timed_run(qc_batch* b, float* ms) {
     if (e != cudaSuccess) rc = qc_cuda_fail(e, "batch run");
     else cudaEventElapsedTime(ms, e0, e1);
   }
+  if (rc == QC_OK) rc = read_status(b);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return rc;
@@ -296,6 +401,10 @@ extern "C" int qc_batch_create(qc_state* const* states, const qc_circuit_desc* c
   b->device = states[0]->device;
   b->stream = (cudaStream_t)o.stream;
   b->htimes.resize(ncirc + 1);
+  std::memset(&b->hctl, 0, sizeof(b->hctl));
+  b->hctl.skip_circ = o.test_skip_circuit > 0 ? o.test_skip_circuit - 1 : -1;
+  b->hctl.skip_member = o.test_skip_member;
+  b->hctl.spin_limit = o.spin_limit > 0 ? (unsigned long long)o.spin_limit : (1ull << 26);
   int rc = QC_OK;
   if (o.fuse_k < 0) {
     // autotune: time the whole batch once per candidate width, keep the fastest
@@ -359,6 +468,7 @@ extern "C" int qc_batch_launch(qc_batch* b, double* completion_ms, double* total
   if (rc == QC_OK && (completion_ms || total_ms)) {
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) rc = qc_cuda_fail(e, "batch run");
+    if (rc == QC_OK) rc = read_status(b);
     if (rc == QC_OK && completion_ms) {
       e = cudaMemcpy(b->htimes.data(), b->dtimes, sizeof(unsigned long long) * (b->ncirc + 1), cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) rc = qc_cuda_fail(e, "cudaMemcpy(times)");

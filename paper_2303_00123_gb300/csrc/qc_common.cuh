@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cstring>
 
 #include "qcgb300.h"
 
@@ -21,6 +22,7 @@ struct qc_state {
   int arith;            // qc_arith for QC_C128
   int device;           // CUDA device ordinal the memory lives on
   int fused_tc;         // 1: complex64 k-qubit blocks (k >= 3) on the tensor cores
+  int packed;           // 1: float-float dense / phase sweeps use packed FP32 pairs
   cudaStream_t stream;  // work queue
 };
 
@@ -271,6 +273,95 @@ struct ArC128x {
     r.re.h = re.s; r.re.l = re.c;
     r.im.h = im.s; r.im.l = im.c;
     return r;
+  }
+};
+
+// complex128 float-float arithmetic with packed FP32 pairs.  Same operations
+// and order as ArC128x, but the real and imaginary accumulators travel
+// together in one 64-bit register pair and every step is one .f32x2
+// instruction (Blackwell executes add/mul/fma on FP32 pairs), which halves the
+// issue slots of the arithmetic.  For a complex term u*x the pairs are
+//   (Re, Im) += (ur, ur) * (xr, xi) + (-ui, ui) * (xi, xr).
+struct ArC128p {
+  static constexpr int V = 2;
+  static constexpr int E = 16;
+  using raw_t = double2;
+  struct val_t { uint64_t h, l; };              // (re.h, im.h), (re.l, im.l)
+  // per complex entry: pairs for the straight term (ur, ur) and the swapped
+  // term (-ui, ui): hi, lo and the negated hi.
+  struct coef_t { uint64_t ah, al, anh, bh, bl, bnh; };
+  static __host__ __device__ uint64_t pk(float lo, float hi) {
+    uint32_t a, b;
+    memcpy(&a, &lo, 4);
+    memcpy(&b, &hi, 4);
+    return (uint64_t)a | ((uint64_t)b << 32);
+  }
+  static __host__ coef_t make_coef(double re, double im) {
+    const float rh = (float)re, rl = (float)(re - (double)rh);
+    const float ih = (float)im, il = (float)(im - (double)ih);
+    coef_t c;
+    c.ah = pk(rh, rh); c.al = pk(rl, rl); c.anh = pk(-rh, -rh);
+    c.bh = pk(-ih, ih); c.bl = pk(-il, il); c.bnh = pk(ih, -ih);
+    return c;
+  }
+  static __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d;
+  }
+  static __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d;
+  }
+  static __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d;
+  }
+  static __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d; asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c)); return d;
+  }
+  static __device__ __forceinline__ uint64_t swp(uint64_t a) { return (a >> 32) | (a << 32); }
+  static __device__ __forceinline__ val_t load(const vec32& v, int e) {
+    const ArC128x::ff re = ArC128x::split(v.w[4 * e], v.w[4 * e + 1]);
+    const ArC128x::ff im = ArC128x::split(v.w[4 * e + 2], v.w[4 * e + 3]);
+    return {pk(re.h, im.h), pk(re.l, im.l)};
+  }
+  static __device__ __forceinline__ float lo32(uint64_t a) { return __uint_as_float((uint32_t)a); }
+  static __device__ __forceinline__ float hi32(uint64_t a) { return __uint_as_float((uint32_t)(a >> 32)); }
+  // x.h = (s_re, s_im), x.l = (c_re, c_im): the double is s + c rounded once.
+  static __device__ __forceinline__ void store(vec32& v, int e, const val_t& x) {
+    const double re = ArC128x::f2d(lo32(x.h)) + ArC128x::f2d(lo32(x.l));
+    const double im = ArC128x::f2d(hi32(x.h)) + ArC128x::f2d(hi32(x.l));
+    v.w[4 * e] = (uint32_t)__double2loint(re); v.w[4 * e + 1] = (uint32_t)__double2hiint(re);
+    v.w[4 * e + 2] = (uint32_t)__double2loint(im); v.w[4 * e + 3] = (uint32_t)__double2hiint(im);
+  }
+  // s, c: running pair sums (see ArC128x::acc_add); en = p - u*x = -(product error)
+  static __device__ __forceinline__ void first(uint64_t& s, uint64_t& c, uint64_t uh, uint64_t ul, uint64_t unh,
+                                               uint64_t xh, uint64_t xl) {
+    const uint64_t p = mul2(uh, xh);
+    const uint64_t en = fma2(unh, xh, p);
+    s = p;
+    c = fma2(ul, xh, fma2(uh, xl, sub2(0ull, en)));
+  }
+  static __device__ __forceinline__ void add(uint64_t& s, uint64_t& c, uint64_t uh, uint64_t ul, uint64_t unh,
+                                             uint64_t xh, uint64_t xl) {
+    const uint64_t p = mul2(uh, xh);
+    const uint64_t en = fma2(unh, xh, p);
+    const uint64_t t = add2(s, p);
+    const uint64_t z = sub2(t, s);
+    const uint64_t err = add2(sub2(s, sub2(t, z)), sub2(p, z));
+    s = t;
+    c = add2(c, sub2(err, en));   // c + (err + e), the scalar form's association
+    c = fma2(uh, xl, c);
+    c = fma2(ul, xh, c);
+  }
+  template <int K>
+  static __device__ __forceinline__ val_t dot(const coef_t* cf, const val_t* x) {
+    uint64_t s, c;
+    first(s, c, cf[0].ah, cf[0].al, cf[0].anh, x[0].h, x[0].l);
+    add(s, c, cf[0].bh, cf[0].bl, cf[0].bnh, swp(x[0].h), swp(x[0].l));
+#pragma unroll
+    for (int k = 1; k < K; k++) {
+      add(s, c, cf[k].ah, cf[k].al, cf[k].anh, x[k].h, x[k].l);
+      add(s, c, cf[k].bh, cf[k].bl, cf[k].bnh, swp(x[k].h), swp(x[k].l));
+    }
+    return {s, c};
   }
 };
 

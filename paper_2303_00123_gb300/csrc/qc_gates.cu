@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "qc_common.cuh"
 
@@ -610,6 +611,9 @@ int launch_dense_t(qc_state* s, const Plan& P, const double* U) {
 
 template <class Ar>
 int launch_dense(qc_state* s, const Plan& P, const double* U) {
+  if constexpr (std::is_same<Ar, ArC128x>::value) {
+    if (s->packed) return launch_dense<ArC128p>(s, P, U);   // same arithmetic, packed FP32 pairs
+  }
   const int key = P.KH * 16 + P.LOWT;
   if constexpr (Ar::V == 2) {
     switch (key) {
@@ -657,6 +661,9 @@ int launch_perm(qc_state* s, const Plan& P) {
 
 template <class Ar>
 int launch_phase(qc_state* s, const Plan& P, const double* z) {
+  if constexpr (std::is_same<Ar, ArC128x>::value) {
+    if (s->packed && phase_kind(z) == 0) return launch_phase<ArC128p>(s, P, z);
+  }
   const int grid = grid_for(P.g.ntiles, kThreads);
   const typename Ar::coef_t c = Ar::make_coef(z[0], z[1]);
   vec32* st = (vec32*)s->ptr;
@@ -697,6 +704,8 @@ int launch_kq_t(qc_state* s, const qc_op& op) {
   static bool attr_set = false;   // per instantiation
   if (!attr_set) {
     QC_CUDA(cudaFuncSetAttribute(k_kq<Ar, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QC_CUDA(cudaFuncSetAttribute(k_kq<Ar, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     attr_set = true;
   }
   k_kq<Ar, K><<<grid_for(g.ngroups, kThreadsK), kThreadsK, smem, s->stream>>>((char*)s->ptr, g, M);
@@ -794,6 +803,8 @@ int launch_fused_t(qc_state* s, const qc_op& op, const GeomF& g, size_t smem) {
   static bool attr_set = false;
   if (!attr_set) {
     QC_CUDA(cudaFuncSetAttribute(k_fused<Ar, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    QC_CUDA(cudaFuncSetAttribute(k_fused<Ar, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     attr_set = true;
   }
   const uint64_t cap = (uint64_t)qc_num_sms() * 8;
@@ -829,6 +840,9 @@ int launch_fused_tc_t(qc_state* s, const qc_op& op, const GeomF& g) {
   static int per_sm = 0;
   if (per_sm == 0) {
     QC_CUDA(cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the default L1/shared split caps residency at one CTA per SM; ask for the full shared memory
+    QC_CUDA(cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tc<K>, kThreadsTC, smem));
     const int ncol = 2 * KR < 32 ? 32 : 2 * KR;
     per_sm = std::max(1, std::min(per_sm, 512 / ncol));   // every resident CTA gets its TMEM columns

@@ -83,6 +83,7 @@ static int new_handle(void* ptr, int n, int dtype, int owned, qc_state** out) {
   s->owned = owned;
   s->arith = QC_ARITH_AUTO;
   s->fused_tc = 1;
+  s->packed = 1;
   s->stream = nullptr;
   cudaGetDevice(&s->device);
   *out = s;
@@ -187,6 +188,12 @@ int qc_set_stream(qc_state* s, void* stream) {
 int qc_set_fused_tc(qc_state* s, int enable) {
   if (!s) return qc_fail(QC_ERR_ARG, "state handle is NULL");
   s->fused_tc = enable ? 1 : 0;
+  return QC_OK;
+}
+
+int qc_set_packed(qc_state* s, int enable) {
+  if (!s) return qc_fail(QC_ERR_ARG, "state handle is NULL");
+  s->packed = enable ? 1 : 0;
   return QC_OK;
 }
 

@@ -53,7 +53,9 @@ class qc_circuit_desc(ctypes.Structure):
 
 
 class qc_batch_opts(ctypes.Structure):
-    _fields_ = [("fuse_k", ctypes.c_int), ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p)]
+    _fields_ = [("fuse_k", ctypes.c_int), ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("spin_limit", ctypes.c_longlong), ("test_skip_circuit", ctypes.c_int),
+                ("test_skip_member", ctypes.c_int)]
 
 
 class qc_grad_opts(ctypes.Structure):
@@ -86,6 +88,7 @@ def _load():
         "qc_set_stream": [P, P],
         "qc_set_arith": [P, I],
         "qc_set_fused_tc": [P, I],
+        "qc_set_packed": [P, I],
         "qc_device_status": [IP],
         "qc_apply_1q": [P, DP, I],
         "qc_apply_c1q": [P, DP, IP, IP, I, I],
@@ -249,6 +252,10 @@ class State:
         """complex64 k>=3 blocks on the tensor cores (default) or CUDA cores."""
         _check(lib.qc_set_fused_tc(self._h, int(bool(enable))))
 
+    def set_packed(self, enable: bool):
+        """complex128 float-float sweeps with packed FP32 pairs (default) or scalar."""
+        _check(lib.qc_set_packed(self._h, int(bool(enable))))
+
     def set_basis(self, x: int = 0):
         _check(lib.qc_state_set_basis(self._h, ctypes.c_uint64(x)))
 
@@ -373,7 +380,8 @@ class Batch:
     """Many independent circuits in one persistent launch (qc_batch_*).
     `states[i]` receives circuits[i] applied to |0...0> at every launch()."""
 
-    def __init__(self, states, circuits, fuse_k: int = -1, use_graph: bool = False, stream=None):
+    def __init__(self, states, circuits, fuse_k: int = -1, use_graph: bool = False, stream=None,
+                 spin_limit: int = 0, test_skip=None):
         if len(states) != len(circuits) or not states:
             raise QCError(QC_ERR_ARG, "states and circuits must be non-empty and of equal length")
         self.states = list(states)
@@ -387,7 +395,9 @@ class Batch:
             descs[i].gates = arr
         hs = (ctypes.c_void_p * len(states))(*[st.handle.value for st in states])
         raw = getattr(stream, "cuda_stream", stream)
-        o = qc_batch_opts(int(fuse_k), int(bool(use_graph)), ctypes.c_void_p(raw or 0))
+        skip_c, skip_m = (test_skip[0] + 1, test_skip[1]) if test_skip else (0, 0)
+        o = qc_batch_opts(int(fuse_k), int(bool(use_graph)), ctypes.c_void_p(raw or 0), int(spin_limit),
+                          int(skip_c), int(skip_m))
         h = ctypes.c_void_p()
         _check(lib.qc_batch_create(hs, descs, len(states), ctypes.byref(o), ctypes.byref(h)))
         self._h = h

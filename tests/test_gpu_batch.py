@@ -102,3 +102,35 @@ def test_batch_full_config_sampled(q):
         got = sts[i].to_numpy().astype(np.complex128)
         assert np.max(np.abs(got - O.run_circuit(n, circs[i]))) <= 2e-5, (i, n, d)
     b.free()
+
+
+def test_batch_teams_match_oracle(q):
+    """States above 8 MB (complex64 n >= 21) are swept by CTA teams with
+    barriers between gate blocks; results against the oracle."""
+    specs = [(21, 30, 501), (22, 25, 502), (12, 40, 503), (23, 12, 504), (16, 30, 505)]
+    circs = [C.random_mix(n, d, seed=s) for n, d, s in specs]
+    sts = make_states(q, [n for n, _, _ in specs], "c64")
+    b = q.Batch(sts, circs, fuse_k=3)
+    comp, tot = b.launch(timing=True)
+    for (n, d, s), st, g in zip(specs, sts, circs):
+        assert np.max(np.abs(st.to_numpy().astype(np.complex128) - O.run_circuit(n, g))) <= 2e-5, n
+    b.free()
+
+
+def test_batch_barrier_timeout_is_reported(q):
+    """A team member that never arrives (host-set test flag) makes the other
+    members' bounded waits give up; the launch returns QC_ERR_TIMEOUT and the
+    device stays usable."""
+    specs = [(22, 10, 601), (10, 10, 602)]
+    circs = [C.random_mix(n, d, seed=s) for n, d, s in specs]
+    sts = make_states(q, [n for n, _, _ in specs], "c64")
+    b = q.Batch(sts, circs, fuse_k=2, spin_limit=20000, test_skip=(0, 1))
+    with pytest.raises(q.QCError) as ei:
+        b.launch(timing=True)
+    assert ei.value.code == q.QC_ERR_TIMEOUT
+    b.free()
+    b2 = q.Batch(sts, circs, fuse_k=2)                 # a normal launch afterwards works
+    b2.launch(timing=True)
+    for (n, d, s), st, g in zip(specs, sts, circs):
+        assert np.max(np.abs(st.to_numpy().astype(np.complex128) - O.run_circuit(n, g))) <= 2e-5
+    b2.free()
