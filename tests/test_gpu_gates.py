@@ -472,3 +472,46 @@ def test_packed_and_scalar_float_float_are_identical(q):
         st.free()
     assert np.array_equal(outs[0], outs[1])
     assert maxerr(outs[0], ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n,dtype", [(33, "c128"), (34, "c64")])
+def test_maximum_size_states(q, n, dtype):
+    """The largest states that fit the GPU's memory (137 GB): a circuit on the
+    qubits {0, n/2, n-1} of a seeded basis state |x>.  Amplitudes factorise:
+    every other qubit keeps x's bit, and the three active qubits follow the
+    oracle's 3-qubit simulation of the same gates (checked on all 8 nonzero
+    amplitudes plus sampled zeros), and the norm stays 1."""
+    import torch
+    a, b, c = 0, n // 2, n - 1
+    gates = [Gate("H", (a,)), Gate("X", (c,), controls=(a,)), Gate("U", (b,), matrix=rand_u(np.random.default_rng(3), 2)),
+             Gate("P", (b,), controls=(c,), theta=0.61), Gate("U4", (c, a), matrix=rand_u(np.random.default_rng(4), 4)),
+             Gate("SWAP", (a, b))]
+    remap = {a: 0, b: 1, c: 2}
+    small = [Gate(g.name, tuple(remap[t] for t in g.qubits), tuple(remap[t] for t in g.controls), g.cstates,
+                  theta=g.theta, matrix=g.matrix) for g in gates]
+    rng = np.random.default_rng(33)
+    x = int(rng.integers(0, 1 << n))
+    bits = lambda v: ((v >> (n - 1 - a)) & 1) * 4 + ((v >> (n - 1 - b)) & 1) * 2 + ((v >> (n - 1 - c)) & 1)
+    ref3 = O.run_circuit(3, small, O.basis_state(3, bits(x)))
+    tdt = torch.complex128 if dtype == "c128" else torch.complex64
+    t = torch.zeros(1 << n, dtype=tdt, device="cuda")
+    st = q.State.from_tensor(t)
+    st.set_basis(x)
+    st.apply_circuit(gates)
+    mask = (1 << (n - 1 - a)) | (1 << (n - 1 - b)) | (1 << (n - 1 - c))
+    ys, ref = [], []
+    for r in range(8):
+        y = (x & ~mask) | (((r >> 2) & 1) << (n - 1 - a)) | (((r >> 1) & 1) << (n - 1 - b)) | ((r & 1) << (n - 1 - c))
+        ys.append(y)
+        ref.append(ref3[r])
+    for _ in range(64):                           # amplitudes that must stay zero
+        y = int(rng.integers(0, 1 << n))
+        if (y & ~mask) != (x & ~mask):
+            ys.append(y)
+            ref.append(0.0)
+    got = t[torch.as_tensor(ys, device="cuda")].cpu().numpy().astype(np.complex128)
+    assert maxerr(got, np.array(ref)) <= (1e-12 if dtype == "c128" else 2e-5)
+    assert abs(st.expect([(1.0, [])]) - 1.0) <= (1e-12 if dtype == "c128" else 1e-5)
+    st.free()
+    del t
+    torch.cuda.empty_cache()
