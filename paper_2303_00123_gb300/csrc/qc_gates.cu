@@ -69,7 +69,7 @@ template <class Ar, int D>
 struct MatD { typename Ar::coef_t m[D * D]; };
 
 template <class Ar, int KH, int LOWT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_dense(vec32* __restrict__ st, const __grid_constant__ Geom g,
         const __grid_constant__ MatD<Ar, (1 << (KH + popc_c(LOWT)))> M) {
   constexpr int KL = popc_c(LOWT);
@@ -843,9 +843,20 @@ int launch_fused_tc_t(qc_state* s, const qc_op& op, const GeomF& g) {
     // the default L1/shared split caps residency at one CTA per SM; ask for the full shared memory
     QC_CUDA(cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared));
-    QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_tc<K>, kThreadsTC, smem));
+    // Residency from the kernel's own footprint (registers in 256-register warp
+    // chunks, shared memory plus the 1 KB the runtime reserves per CTA) and the
+    // tensor-memory columns each CTA allocates.
+    cudaFuncAttributes fa;
+    QC_CUDA(cudaFuncGetAttributes(&fa, k_fused_tc<K>));
+    int dev = 0, smem_sm = 0, regs_sm = 0;
+    QC_CUDA(cudaGetDevice(&dev));
+    QC_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    QC_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_sm / (warp_regs * (kThreadsTC / 32));
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
     const int ncol = 2 * KR < 32 ? 32 : 2 * KR;
-    per_sm = std::max(1, std::min(per_sm, 512 / ncol));   // every resident CTA gets its TMEM columns
+    per_sm = std::max(1, std::min(std::min(by_regs, by_smem), std::min(512 / ncol, 2048 / kThreadsTC)));
   }
   const uint64_t cap = (uint64_t)qc_num_sms() * per_sm;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
