@@ -405,7 +405,7 @@ def run_fused_case(args):
     n = args.n
     dt = q.C64 if args.dtype == "c64" else q.C128
     elem = 8 if dt == q.C64 else 16
-    gates = C.brickwork(n, BRICK_DEPTH, seed=SEED_BRICK)
+    gates = C.qft(n) if args.circuit == "qft" else C.brickwork(n, BRICK_DEPTH, seed=SEED_BRICK)
     t = torch.empty(1 << n, dtype=torch.complex64 if dt == q.C64 else torch.complex128, device="cuda")
     st = q.State.from_tensor(t)
     st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
@@ -436,7 +436,7 @@ def run_fused_case(args):
     if args.n_err > 0:
         from oracle import oracle as O
         ne = args.n_err
-        g2 = C.brickwork(ne, BRICK_DEPTH, seed=SEED_BRICK)
+        g2 = C.qft(ne) if args.circuit == "qft" else C.brickwork(ne, BRICK_DEPTH, seed=SEED_BRICK)
         ref = O.run_circuit(ne, g2)
         for k in (0, 2, 3, 4, 5):
             s2 = q.State(ne, dt)
@@ -447,7 +447,8 @@ def run_fused_case(args):
             s2.free()
             err[str(k)] = {"max_abs": float(np.max(np.abs(got - ref))),
                            "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
-    print(json.dumps({"case": "fused", "n": n, "dtype": args.dtype, "arith": args.arith, "gates": len(gates),
+    print(json.dumps({"case": "fused", "circuit": args.circuit, "n": n, "dtype": args.dtype, "arith": args.arith,
+                      "gates": len(gates),
                       "tensor_cores": (not args.no_tc) and args.dtype == "c64",
                       "by_fuse_k": res, "n_err": args.n_err, "error_vs_oracle": err,
                       "speedup_best_vs_unfused": round(res["0"]["ms"] / min(v["ms"] for v in res.values()), 2)}))
@@ -524,6 +525,15 @@ def extra_measurements(q, st, stream, brick, x):
     t2 = _event_ms(stream, lambda: brick_run(st, 2))
     fused["c128_k2"] = {"ms": round(t2, 1), "unfused_ms": round(t0, 1), "speedup": round(t0 / t2, 2),
                         "launches": len(q.fuse_plan(N_QUBITS, brick, 2))}
+    qft = C.qft(N_QUBITS)
+    def qft_run(k):
+        st.set_basis(x)
+        st.apply_circuit(qft, fuse_k=k)
+    qft_run(2)
+    q0 = _event_ms(stream, lambda: qft_run(0))
+    q2 = _event_ms(stream, lambda: qft_run(2))
+    fused["qft_c128_k2_phase_runs"] = {"ms": round(q2, 1), "unfused_ms": round(q0, 1), "speedup": round(q0 / q2, 2),
+                                       "launches": len(q.fuse_plan(N_QUBITS, qft, 2))}
     t64 = torch.empty(1 << N_QUBITS, dtype=torch.complex64, device="cuda")
     s64 = q.State.from_tensor(t64)
     s64.set_stream(stream)
@@ -535,7 +545,7 @@ def extra_measurements(q, st, stream, brick, x):
     s64.free()
     del t64
     torch.cuda.empty_cache()
-    out["fused"] = {"workload": "brickwork depth 40, n=30, greedy fusion", **fused}
+    out["fused"] = {"workload": "n=30: brickwork depth 40 (greedy k-qubit blocks); QFT (linear phase runs)", **fused}
     # batched: 1024 circuits, one persistent launch vs one launch per gate
     specs = C.batch_specs(1024, seed=4)
     circs = [C.random_mix(n, d, seed=sd) for n, d, sd in specs]
@@ -640,6 +650,7 @@ def main():
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--n-err", dest="n_err", type=int, default=0)
+    ap.add_argument("--circuit", default="brickwork", choices=["brickwork", "qft"])
     ap.add_argument("--no-tc", dest="no_tc", action="store_true", help="complex64 blocks on CUDA cores")
     ap.add_argument("--no-packed", dest="no_packed", action="store_true", help="scalar FP32 float-float")
     args = ap.parse_args()

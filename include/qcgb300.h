@@ -180,7 +180,9 @@ typedef struct {
 
 typedef struct {
   int fuse_k;      /* 0 or 1: apply gate by gate; 2..5: greedy fusion into
-                      k-qubit blocks applied as dense k-qubit gates */
+                      k-qubit blocks applied as dense k-qubit gates, and runs
+                      of commuting phase gates sharing a qubit applied as one
+                      linear-phase sweep (qc_block kind 1) */
   int use_graph;   /* 1: capture the launches in a CUDA graph and replay it */
   float* gate_ms;  /* optional host array of at least ngates entries: entry i
                       receives the device time (ms) of launch i (a gate or a
@@ -194,8 +196,13 @@ typedef struct {
  * one to the state).  opts may be NULL (defaults: no fusion, no graph). */
 int qc_apply_circuit(qc_state* s, const qc_gate* gates, int ngates, const qc_opts* opts);
 
-/* A k-qubit block produced by the fusion planner: dense U on `qubits`
- * (qubits[0] = MSB of U's index), applied only where the controls hold. */
+/* One launch of a fusion plan.  kind 0: dense U on `qubits` (qubits[0] =
+ * MSB of U's index), applied only where the controls hold.  kind 1: a run of
+ * commuting phase gates that all involve qubit `anchor` (for instance the
+ * controlled phases of one QFT stage, Fig. 1), applied in one sweep:
+ * amplitudes whose anchor bit is 1 are multiplied by
+ * exp(i (theta0 + sum_j bit(lin_qubits[j]) * lin_theta[j])). */
+#define QC_MAX_LIN 36
 typedef struct {
   int k;
   int qubits[QC_MAX_TARGETS];
@@ -203,6 +210,12 @@ typedef struct {
   int controls[QC_MAX_CONTROLS];
   int cstates[QC_MAX_CONTROLS];
   double U[2 * 32 * 32];            /* 2^k x 2^k complex, row-major (re, im) */
+  int kind;                         /* 0: matrix block, 1: linear phase run */
+  int anchor;
+  int nlin;
+  int lin_qubits[QC_MAX_LIN];
+  double lin_theta[QC_MAX_LIN];
+  double theta0;
 } qc_block;
 
 /* Host-only: the launch plan qc_apply_circuit would execute for these gates

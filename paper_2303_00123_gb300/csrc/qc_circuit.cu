@@ -73,6 +73,7 @@ int resolve(int n, const qc_gate& g, Resolved& R) {
 }
 
 void to_op(int n, const Resolved& R, qc_op& op) {
+  op.kind = QC_OP_MATRIX;
   op.k = R.k;
   op.nc = R.nc;
   for (int i = 0; i < R.k; i++) op.tpos[i] = n - 1 - R.t[i];
@@ -247,16 +248,52 @@ int qc_gate_to_op(int n, const qc_gate& g, qc_op& op) {
 }
 
 namespace {
-int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops);
+int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops, bool phase_runs);
 }
 
-int qc_plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops) {
-  return plan_ops(n, gates, ngates, fuse_k, ops);
+int qc_plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops, bool phase_runs) {
+  return plan_ops(n, gates, ngates, fuse_k, ops, phase_runs);
 }
 
 namespace {
+// A (controlled) phase gate whose phase applies when all of its qubits are 1:
+// diag(1, e^{i theta}) on the target, controls in state 1.  Returns the qubit
+// set (1 or 2 qubits) and theta, or false.
+bool phase_gate(const Resolved& R, int* qs, int* nq, double* theta) {
+  if (R.k != 1 || R.nc > 1) return false;
+  for (int i = 0; i < R.nc; i++) if (R.cs[i] != 1) return false;
+  const cd u00 = R.U[0], u01 = R.U[1], u10 = R.U[2], u11 = R.U[3];
+  if (u01 != cd(0) || u10 != cd(0) || u00 != cd(1)) return false;
+  if (std::abs(std::abs(u11) - 1.0) > 1e-14) return false;
+  *theta = std::arg(u11);
+  *nq = 0;
+  qs[(*nq)++] = R.t[0];
+  for (int i = 0; i < R.nc; i++) qs[(*nq)++] = R.c[i];
+  return true;
+}
+
+void emit_matrix_segment(int n, const std::vector<Resolved>& res, int begin, int end, int fuse_k,
+                         std::vector<qc_op>& ops) {
+  if (begin >= end) return;
+  std::vector<Resolved> seg(res.begin() + begin, res.begin() + end);
+  std::vector<Emitted> em;
+  fuse(n, seg, std::min(fuse_k, n), em);
+  for (size_t i = 0; i < em.size(); i++) {
+    qc_op op;
+    if (em[i].single) { to_op(n, seg[em[i].gate], op); ops.push_back(op); continue; }
+    const Block& b = em[i].block;
+    Resolved R;
+    R.k = (int)b.q.size();
+    R.nc = 0;
+    for (int j = 0; j < R.k; j++) R.t[j] = b.q[j];
+    R.U = b.M;
+    to_op(n, R, op);
+    ops.push_back(op);
+  }
+}
+
 // Build the launch plan (shared by qc_apply_circuit, qc_fuse_plan and the batch path).
-int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops) {
+int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops, bool phase_runs) {
   if (ngates < 0 || (ngates > 0 && !gates)) return qc_fail(QC_ERR_ARG, "invalid gate list");
   if (fuse_k < 0 || fuse_k > QC_MAX_TARGETS) return qc_fail(QC_ERR_ARG, "fuse_k=%d out of range 0..5", fuse_k);
   std::vector<Resolved> res(ngates);
@@ -264,19 +301,65 @@ int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc
     if (int rc = resolve(n, gates[i], res[i])) return qc_fail(rc, "gate %d: %s", i, qc_last_error());
   ops.clear();
   if (fuse_k >= 2) {
-    std::vector<Emitted> em;
-    fuse(n, res, std::min(fuse_k, n), em);
-    ops.resize(em.size());
-    for (size_t i = 0; i < em.size(); i++) {
-      if (em[i].single) { to_op(n, res[em[i].gate], ops[i]); continue; }
-      const Block& b = em[i].block;
-      Resolved R;
-      R.k = (int)b.q.size();
-      R.nc = 0;
-      for (int j = 0; j < R.k; j++) R.t[j] = b.q[j];
-      R.U = b.M;
-      to_op(n, R, ops[i]);
+    int seg_begin = 0;
+    int i = 0;
+    while (i < ngates) {
+      // longest run of phase gates from i that share a qubit (the anchor)
+      int qs[2], nq;
+      double th;
+      int j = i;
+      uint64_t common = 0;
+      if (phase_runs && phase_gate(res[i], qs, &nq, &th)) {
+        common = 0;
+        for (int t = 0; t < nq; t++) common |= 1ull << qs[t];
+        j = i + 1;
+        std::vector<int> lin;
+        while (j < ngates && phase_gate(res[j], qs, &nq, &th)) {
+          uint64_t s = 0;
+          for (int t = 0; t < nq; t++) s |= 1ull << qs[t];
+          if (!(common & s)) break;
+          const uint64_t c2 = common & s;
+          // distinct linear qubits (all but the anchor) must stay within QC_MAX_LIN
+          int distinct = 0;
+          uint64_t seen = 0;
+          for (int g = i; g <= j; g++) {
+            int q2[2], n2;
+            double t2;
+            phase_gate(res[g], q2, &n2, &t2);
+            for (int t = 0; t < n2; t++) seen |= 1ull << q2[t];
+          }
+          distinct = __builtin_popcountll(seen) - 1;
+          if (distinct > QC_MAX_LIN) break;
+          common = c2;
+          j++;
+        }
+      }
+      if (j - i >= 2) {
+        emit_matrix_segment(n, res, seg_begin, i, fuse_k, ops);
+        const int anchor = __builtin_ctzll(common);   // a qubit shared by every gate of the run
+        qc_op op;
+        std::memset(&op, 0, sizeof(op));
+        op.kind = QC_OP_LINEAR_PHASE;
+        op.anchor = n - 1 - anchor;
+        double lin[64] = {0};
+        uint64_t linmask = 0;
+        for (int g = i; g < j; g++) {
+          phase_gate(res[g], qs, &nq, &th);
+          int other = -1;
+          for (int t = 0; t < nq; t++) if (qs[t] != anchor) other = qs[t];
+          if (other < 0) op.theta0 += th;
+          else { lin[other] += th; linmask |= 1ull << other; }
+        }
+        for (int q = 0; q < n; q++)
+          if ((linmask >> q) & 1) { op.lin_pos[op.nlin] = n - 1 - q; op.lin_theta[op.nlin] = lin[q]; op.nlin++; }
+        ops.push_back(op);
+        i = j;
+        seg_begin = j;
+      } else {
+        i++;
+      }
     }
+    emit_matrix_segment(n, res, seg_begin, ngates, fuse_k, ops);
   } else {
     ops.resize(ngates);
     for (int i = 0; i < ngates; i++) to_op(n, res[i], ops[i]);
@@ -290,7 +373,7 @@ extern "C" int qc_fuse_plan(int n, const qc_gate* gates, int ngates, int fuse_k,
   if (n < 1 || n > 36) return qc_fail(QC_ERR_ARG, "n=%d out of range 1..36", n);
   if (!nblocks) return qc_fail(QC_ERR_ARG, "nblocks is NULL");
   std::vector<qc_op> ops;
-  if (int rc = plan_ops(n, gates, ngates, fuse_k, ops)) return rc;
+  if (int rc = plan_ops(n, gates, ngates, fuse_k, ops, true)) return rc;
   *nblocks = (int)ops.size();
   if ((int)ops.size() > max_blocks || (!blocks && !ops.empty()))
     return qc_fail(QC_ERR_ARG, "plan needs %d blocks, buffer holds %d", (int)ops.size(), max_blocks);
@@ -298,6 +381,14 @@ extern "C" int qc_fuse_plan(int n, const qc_gate* gates, int ngates, int fuse_k,
     const qc_op& op = ops[i];
     qc_block& b = blocks[i];
     std::memset(&b, 0, sizeof(b));
+    if (op.kind == QC_OP_LINEAR_PHASE) {
+      b.kind = 1;
+      b.anchor = n - 1 - op.anchor;
+      b.nlin = op.nlin;
+      for (int j = 0; j < op.nlin; j++) { b.lin_qubits[j] = n - 1 - op.lin_pos[j]; b.lin_theta[j] = op.lin_theta[j]; }
+      b.theta0 = op.theta0;
+      continue;
+    }
     b.k = op.k;
     for (int j = 0; j < op.k; j++) b.qubits[j] = n - 1 - op.tpos[j];
     b.nc = op.nc;
@@ -316,7 +407,7 @@ extern "C" int qc_apply_circuit(qc_state* s, const qc_gate* gates, int ngates, c
   if (o.use_graph && s->stream == nullptr) return qc_fail(QC_ERR_ARG, "graph capture needs a non-default stream (qc_set_stream)");
 
   std::vector<qc_op> ops;
-  if (int rc = plan_ops(s->n, gates, ngates, o.fuse_k, ops)) return rc;
+  if (int rc = plan_ops(s->n, gates, ngates, o.fuse_k, ops, true)) return rc;
   if (o.nlaunch) *o.nlaunch = (int)ops.size();
 
   std::vector<cudaEvent_t> ev;

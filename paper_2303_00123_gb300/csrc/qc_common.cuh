@@ -370,13 +370,24 @@ struct ArC128p {
 // --------------------------------------------------------------------------
 enum qc_struct { QC_ST_DENSE = 0, QC_ST_PERM = 1, QC_ST_PHASE = 2 };
 
+enum qc_op_kind { QC_OP_MATRIX = 0, QC_OP_LINEAR_PHASE = 1 };
+
 struct qc_op {
+  int kind;                     // qc_op_kind
   int k;                        // number of targets
   int tpos[QC_MAX_TARGETS];     // target bit positions, tpos[0] = MSB of U's index
   int nc;                       // controls
   int cpos[QC_MAX_CONTROLS];    // control bit positions
   int cval[QC_MAX_CONTROLS];    // control states
   double U[2 * 32 * 32];        // 2^k x 2^k complex, row-major (re, im)
+  // QC_OP_LINEAR_PHASE: amplitudes whose `anchor` bit is 1 are multiplied by
+  // exp(i (theta0 + sum_j bit_{lin_pos[j]} * lin_theta[j])) -- a run of
+  // commuting (controlled) phase gates that all involve the anchor qubit.
+  int anchor;
+  int nlin;
+  int lin_pos[QC_MAX_LIN];
+  double lin_theta[QC_MAX_LIN];
+  double theta0;
 };
 
 // Resolve a gate record (named or explicit matrix) into an op: validates the
@@ -386,9 +397,12 @@ int qc_gate_to_op(int n, const qc_gate& g, qc_op& op);
 // Number of tensor-core tile waits that gave up (device counter; 0 normally).
 int qc_tc_timeouts(int* count);
 
-// Launch plan of a circuit: one op per gate, or per fused block (fuse_k >= 2).
+// Launch plan of a circuit: one op per gate, or per fused block (fuse_k >= 2);
+// with phase_runs, runs of commuting phase gates sharing a qubit become one
+// QC_OP_LINEAR_PHASE op.
 #include <vector>
-int qc_plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops);
+int qc_plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops,
+                bool phase_runs = false);
 
 // Apply one (controlled) k-qubit gate given by its matrix; the launcher
 // classifies the matrix (dense / permutation / diagonal) and picks a kernel.

@@ -537,6 +537,66 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL) : "memory");
 }
 
+// ---------------------------------------------------------------- linear phase runs
+// A run of commuting phase gates that all involve one qubit (the QFT's
+// controlled phases after each Hadamard, Fig. 1) is one diagonal operator:
+// amplitudes with the anchor bit set get exp(i (theta0 + sum_j b_j theta_j)).
+// The linear bits are split into groups of at most 8; table g holds the 2^m
+// partial phases of group g (host FP64, theta0 folded into table 0), so an
+// amplitude needs one table entry per group and a few complex products in the
+// state's arithmetic.  Only the half of the state with the anchor bit set is
+// read and written.
+constexpr int kLinGroups = 5;
+struct LinGeom {
+  Geom g;                        // vectors with the anchor bit set
+  int ngroups;
+  int gbits[kLinGroups];         // bits per group
+  int gcontig[kLinGroups];       // 1: positions gpos[g][0], +1, ... (one shift and mask)
+  int gpos[kLinGroups][8];       // bit positions (amplitude index), lowest table bit first
+  int toff[kLinGroups];          // first entry of group g in the table
+};
+
+constexpr int kLinTab = 4 * 256 + 16;   // 36 linear bits: groups of 8, 8, 8, 8, 4
+
+template <class Ar>
+struct LinTab { typename Ar::coef_t t[kLinTab]; };
+
+template <class Ar>
+__global__ void __launch_bounds__(kThreads)
+k_linear_phase(vec32* __restrict__ st, const __grid_constant__ LinGeom lg, const __grid_constant__ LinTab<Ar> tab,
+               int ntab) {
+  constexpr int V = Ar::V;
+  constexpr int L = V == 4 ? 2 : 1;
+  using val_t = typename Ar::val_t;
+  using coef_t = typename Ar::coef_t;
+  __shared__ coef_t T[kLinTab];        // lookups diverge across a warp: shared, not constant, memory
+  for (int i = threadIdx.x; i < ntab; i += kThreads) T[i] = tab.t[i];
+  __syncthreads();
+  const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+  for (uint64_t j = (uint64_t)blockIdx.x * kThreads + threadIdx.x; j < lg.g.ntiles; j += stride) {
+    const uint64_t v = tile_base(lg.g, j);
+    vec32 x = qc_ld32(st + v);
+#pragma unroll
+    for (int e = 0; e < V; e++) {
+      if ((e & lg.g.lowc_mask) != lg.g.lowc_val) continue;
+      const uint64_t y = (v << L) | (uint64_t)e;
+      val_t a = Ar::load(x, e);
+      for (int g = 0; g < lg.ngroups; g++) {
+        uint32_t m;
+        if (lg.gcontig[g]) {
+          m = (uint32_t)(y >> lg.gpos[g][0]) & ((1u << lg.gbits[g]) - 1u);
+        } else {
+          m = 0;
+          for (int b = 0; b < lg.gbits[g]; b++) m |= (uint32_t)((y >> lg.gpos[g][b]) & 1u) << b;
+        }
+        a = Ar::template dot<1>(&T[lg.toff[g] + m], &a);
+      }
+      Ar::store(x, e, a);
+    }
+    qc_st32(st + v, x);
+  }
+}
+
 // ---------------------------------------------------------------- host side
 inline int grid_for(uint64_t work, int threads) {
   const uint64_t want = (work + threads - 1) / threads;
@@ -880,6 +940,50 @@ int launch_fused_tc(qc_state* s, const qc_op& op, bool* done) {
   }
 }
 
+
+template <class Ar>
+int launch_linear_phase(qc_state* s, const qc_op& op) {
+  constexpr int L = Ar::V == 4 ? 2 : 1;
+  LinGeom lg;
+  std::memset(&lg, 0, sizeof(lg));
+  int cpos[1] = {op.anchor}, cval[1] = {1};
+  Plan P;
+  if (int rc = build_geom(s, L, nullptr, 0, cpos, cval, 1, P)) return rc;
+  lg.g = P.g;
+  // groups of <= 8 linear bits, in ascending position order
+  int order[QC_MAX_LIN];
+  for (int i = 0; i < op.nlin; i++) order[i] = i;
+  std::sort(order, order + op.nlin, [&](int a, int b) { return op.lin_pos[a] < op.lin_pos[b]; });
+  lg.ngroups = (op.nlin + 7) / 8;
+  if (lg.ngroups > kLinGroups) return qc_fail(QC_ERR_ARG, "internal: %d linear bits", op.nlin);
+  if (lg.ngroups == 0) lg.ngroups = 1;   // theta0 only: a one-entry table
+  std::vector<typename Ar::coef_t> tab;
+  for (int g = 0; g < lg.ngroups; g++) {
+    const int b0 = g * 8, nb = std::min(8, std::max(0, op.nlin - b0));
+    lg.gbits[g] = nb;
+    lg.toff[g] = (int)tab.size();
+    bool contig = true;
+    for (int b = 0; b < nb; b++) {
+      lg.gpos[g][b] = op.lin_pos[order[b0 + b]];
+      if (b > 0 && lg.gpos[g][b] != lg.gpos[g][b - 1] + 1) contig = false;
+    }
+    lg.gcontig[g] = contig ? 1 : 0;
+    if (nb == 0) lg.gpos[g][0] = 0;
+    for (int m = 0; m < (1 << nb); m++) {
+      double ph = g == 0 ? op.theta0 : 0.0;
+      for (int b = 0; b < nb; b++) if ((m >> b) & 1) ph += op.lin_theta[order[b0 + b]];
+      tab.push_back(Ar::make_coef(std::cos(ph), std::sin(ph)));
+    }
+  }
+  if (tab.size() > (size_t)kLinTab) return qc_fail(QC_ERR_ARG, "internal: phase table of %zu entries", tab.size());
+  LinTab<Ar> T;
+  std::memcpy(T.t, tab.data(), tab.size() * sizeof(typename Ar::coef_t));
+  k_linear_phase<Ar><<<grid_for(lg.g.ntiles, kThreads), kThreads, 0, s->stream>>>((vec32*)s->ptr, lg, T,
+                                                                                  (int)tab.size());
+  QC_LAUNCHED("k_linear_phase");
+  return QC_OK;
+}
+
 // Reorder a 2-qubit matrix so that its first target has the higher bit position.
 void order_two_qubit(qc_op& op) {
   if (op.k != 2 || op.tpos[0] > op.tpos[1]) return;
@@ -955,6 +1059,12 @@ int qc_tc_timeouts(int* count) {
 }
 
 int qc_launch_op(qc_state* s, const qc_op& op) {
+  if (op.kind == QC_OP_LINEAR_PHASE) {
+    if (s->n < 3) return qc_fail(QC_ERR_ARG, "internal: linear phase op on n < 3");
+    if (s->dtype == QC_C64) return launch_linear_phase<ArC64>(s, op);
+    if (s->arith == QC_ARITH_NATIVE) return launch_linear_phase<ArC128>(s, op);
+    return launch_linear_phase<ArC128x>(s, op);
+  }
   if (s->dtype == QC_C64) return dispatch<ArC64>(s, op);
   if (s->arith == QC_ARITH_NATIVE) return dispatch<ArC128>(s, op);
   return dispatch<ArC128x>(s, op);

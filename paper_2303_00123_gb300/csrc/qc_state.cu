@@ -1,4 +1,5 @@
 // qc_state.cu -- state handles, errors, single-gate C entry points.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -216,6 +217,7 @@ static int apply_generic(qc_state* s, const double* U, const int* targets, int k
   if (!targets) return qc_fail(QC_ERR_ARG, "targets is NULL");
   if (int rc = qc_check_qubits(s->n, targets, k, controls, cstates, nc)) return rc;
   qc_op op;
+  op.kind = QC_OP_MATRIX;
   op.k = k;
   for (int i = 0; i < k; i++) op.tpos[i] = bitpos(s->n, targets[i]);
   op.nc = nc;

@@ -42,10 +42,15 @@ class qc_opts(ctypes.Structure):
                 ("gate_ms", ctypes.POINTER(ctypes.c_float)), ("nlaunch", ctypes.POINTER(ctypes.c_int))]
 
 
+MAX_LIN = 36
+
+
 class qc_block(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("qubits", ctypes.c_int * MAX_TARGETS), ("nc", ctypes.c_int),
                 ("controls", ctypes.c_int * MAX_CONTROLS), ("cstates", ctypes.c_int * MAX_CONTROLS),
-                ("U", ctypes.c_double * (2 * 32 * 32))]
+                ("U", ctypes.c_double * (2 * 32 * 32)), ("kind", ctypes.c_int), ("anchor", ctypes.c_int),
+                ("nlin", ctypes.c_int), ("lin_qubits", ctypes.c_int * MAX_LIN),
+                ("lin_theta", ctypes.c_double * MAX_LIN), ("theta0", ctypes.c_double)]
 
 
 class qc_circuit_desc(ctypes.Structure):
@@ -323,7 +328,9 @@ class State:
 
 
 def fuse_plan(n: int, gates, fuse_k: int):
-    """Host-only launch plan: list of (qubits, controls, cstates, U) blocks."""
+    """Host-only launch plan: a list with one entry per launch, either a
+    matrix block (qubits, controls, cstates, U) or a linear phase run
+    ("phase", anchor, [(qubit, theta), ...], theta0)."""
     arr, keep = gate_records(gates)
     nb = ctypes.c_int(0)
     cap = max(1, len(gates))
@@ -331,6 +338,9 @@ def fuse_plan(n: int, gates, fuse_k: int):
     _check(lib.qc_fuse_plan(n, arr, len(gates), int(fuse_k), blocks, cap, ctypes.byref(nb)))
     out = []
     for b in blocks[:nb.value]:
+        if b.kind == 1:
+            out.append(("phase", b.anchor, [(b.lin_qubits[j], b.lin_theta[j]) for j in range(b.nlin)], b.theta0))
+            continue
         d = 1 << b.k
         U = np.array(b.U[:2 * d * d], dtype=np.float64).view(np.complex128).reshape(d, d)
         out.append((tuple(b.qubits[:b.k]), tuple(b.controls[:b.nc]), tuple(b.cstates[:b.nc]), U.copy()))

@@ -515,3 +515,25 @@ def test_maximum_size_states(q, n, dtype):
     st.free()
     del t
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_fused_qft_with_linear_phase_runs(q, mode):
+    """QFT with fusion: each stage's controlled phases run as one linear-phase
+    sweep; against the DFT and the oracle, n = 6, 13, 17 (phase bits in and
+    above a vector, anchors at every position)."""
+    for n in (6, 13, 17):
+        x = (0x5A5A5 * 7 + n) % (1 << n)
+        got = gpu_run(q, n, C.qft(n), mode, psi0=O.basis_state(n, x), fuse_k=4)
+        e = np.zeros(1 << n)
+        e[x] = 1
+        assert maxerr(got, np.fft.fft(e) / math.sqrt(1 << n)) <= TOL[mode], n
+    # runs with scattered linear qubits, a theta0 term and a Z, on a random state
+    n = 11
+    rng = np.random.default_rng(8)
+    gates = [Gate("H", (q_,)) for q_ in range(n)]
+    gates += [Gate("P", (4,), controls=(int(c),), theta=float(rng.uniform(-3, 3))) for c in (0, 9, 2, 10, 7, 5, 1)]
+    gates += [Gate("P", (4,), theta=0.37), Gate("Z", (6,), controls=(4,)), Gate("U", (3,), matrix=rand_u(rng, 2))]
+    gates += [Gate("P", (int(t),), controls=(8,), theta=float(rng.uniform(-3, 3))) for t in (0, 10, 3, 2)]
+    phi = C.random_state(n, 5)
+    assert maxerr(gpu_run(q, n, gates, mode, psi0=phi, fuse_k=3), O.run_circuit(n, gates, phi)) <= TOL[mode]
