@@ -135,9 +135,15 @@ class ClockSampler:
 
 
 def kernel_sources_sha():
+    """Fingerprint of the dense-sweep kernel: the arithmetic header and the
+    k_dense section of qc_gates.cu (other kernels in the file do not count)."""
     h = hashlib.sha256()
-    for f in ("qc_common.cuh", "qc_gates.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2303_00123_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2303_00123_gb300", "csrc")
+    h.update(open(os.path.join(csrc, "qc_common.cuh"), "rb").read())
+    g = open(os.path.join(csrc, "qc_gates.cu")).read()
+    a = g.index("// ---------------------------------------------------------------- dense")
+    b = g.index("// ---------------------------------------------------------------- permutation")
+    h.update(g[a:b].encode())
     return h.hexdigest()[:16]
 
 
@@ -454,10 +460,39 @@ def run_fused_case(args):
                       "speedup_best_vs_unfused": round(res["0"]["ms"] / min(v["ms"] for v in res.values()), 2)}))
 
 
+def run_expect_case(args):
+    """qc_expect of the TFIM chain (n-1 ZZ terms in one diagonal sweep, n X
+    terms in one sweep each) on a seeded n-qubit state: time and algorithmic
+    GB/s (every sweep reads the whole state once)."""
+    import torch
+    from paper_2303_00123_gb300 import qcgb300 as q
+    n = args.n
+    dt = q.C64 if args.dtype == "c64" else q.C128
+    elem = 8 if dt == q.C64 else 16
+    st = q.State(n, dt)
+    st.apply_circuit([C.Gate("H", (i,)) for i in range(n)] + C.random_mix(n, 20, seed=3))
+    H = C.tfim(n, 1.0)
+    for _ in range(args.warmup):
+        st.expect(H)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e = st.expect(H)
+    dt_s = (time.perf_counter() - t0) / args.steps
+    sweeps = 1 + n
+    gbps = sweeps * (1 << n) * elem / dt_s / 1e9
+    peak, _ = measured_peaks()
+    print(json.dumps({"case": "expect", "n": n, "dtype": args.dtype, "terms": len(H), "sweeps": sweeps,
+                      "ms": round(dt_s * 1e3, 2), "GBps": round(gbps, 1), "frac_of_measured_hbm": round(gbps / peak, 4),
+                      "energy": e}))
+    st.free()
+
+
 def run_case(args):
     """Per-target-qubit timing of one gate kind on an n-qubit state."""
     import torch
     from paper_2303_00123_gb300 import qcgb300 as q
+    if args.case == "expect":
+        return run_expect_case(args)
     if args.case == "adjoint":
         return run_adjoint_case(args)
     if args.case == "batch":
