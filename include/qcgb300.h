@@ -285,6 +285,14 @@ typedef struct {
  * modified. */
 int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out);
 
+/* Host only: the number of passes qc_expect makes over an n-qubit state of
+ * the given dtype for H.  A pass reads the state once, a tile of 2^12
+ * (complex128) or 2^13 (complex64) amplitudes at a time, and evaluates every
+ * term whose X/Y qubits fall in the span of the tile's bits; the tiles' bits
+ * are chosen per pass so that few passes cover all terms.  Validates H like
+ * qc_expect (QC_ERR_ARG on a malformed sum); an empty sum needs 0 passes. */
+int qc_expect_passes(int n, int dtype, const qc_pauli_sum* H, int* npasses);
+
 /* Same result as qc_expect, for callers that cannot allocate device memory
  * -- for instance an application whose own memory manager (a framework's
  * caching allocator) has already reserved the whole device, or a

@@ -1,14 +1,17 @@
-// qc_expect.cu -- <psi| sum_t c_t P_t |psi> for Pauli sums, FP64 reductions.
+// qc_expect.cu -- <psi| sum_t c_t P_t |psi> for Pauli sums.
 //
 // For a Pauli string P with flip mask F (its X and Y qubits), phase mask
 // Q (its Y and Z qubits) and nY Y factors, P|y> = i^nY (-1)^popc(y & Q) |y^F>
 // (X|b> = |1-b>, Y|b> = i(-1)^b |1-b>, Z|b> = (-1)^b |b>), so
 //   <psi|P|psi> = sum_y i^nY (-1)^popc(y & Q) conj(psi_{y^F}) psi_y .
-// Terms that share F are evaluated in one sweep: the kernel visits each pair
-// {y, y^F} once (y with the pivot bit of F clear), forms the overlap products
-// and adds every term's signed contribution to an FP64 accumulator.  Per-block
-// partial sums go to device scratch memory; a single-block kernel adds them up
-// in a fixed order, so the result is deterministic.
+// qc_expect evaluates the sum in tiled passes (k_pauli_tile, below): each
+// pass covers every term whose flip mask lies in the span of its tile bits.
+// qc_expect_noalloc keeps the simpler form, one sweep per distinct flip mask
+// (k_pauli_sweep): the sweep visits each pair {y, y^F} once (y with the
+// pivot bit of F clear), forms the overlap products and adds every term's
+// signed contribution to an FP64 accumulator.  Either way per-block partial
+// sums go to device memory and a single-block kernel adds them up in a fixed
+// order, so the result is deterministic.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -126,13 +129,375 @@ int get_scratch(int device, size_t bytes, void** p) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// qc_expect: tiled passes.
+//
+// A pass reads the state once, one tile at a time.  A tile is a set of 2^L
+// basis indices y = base ^ G(hc) ^ low: `low` runs over the m lowest bits,
+// hc over h bits that select a combination G(hc) of h generator masks (each
+// with its own pivot bit at or above m, no generator containing another's
+// pivot), and `base` over the remaining bits (zero at the low and pivot
+// bits).  With the local index l = hc << m | low a term with flip mask F maps
+// the tile onto itself whenever F lies in the span of the low bits and the
+// generators: then y ^ F = base ^ G(hc ^ hc_F) ^ (low ^ F_low), i.e. the local
+// index l ^ FL with FL = hc_F << m | F_low.  The sign splits the same way:
+// popc(y & Q) = popc(base & Q) + popc(l & QL) (mod 2) with QL = q_hc << m |
+// (Q & low mask), bit i of q_hc being the parity of G_i & Q.  So one pass,
+// tile by tile in shared memory, evaluates every term whose flip mask lies in
+// its span; the host chooses the generators so that few passes cover all
+// terms (for nearest-neighbour Hamiltonians on 30 qubits: 4 passes instead of
+// one sweep per distinct flip mask).
+//
+// Arithmetic.  The sweeps run in FP32 error-free transformations (GB300's
+// FP64 rate is far below its FP32 rate): amplitudes are split into hi + lo
+// floats (complex128: 47 significant bits; complex64: exact), products are
+// TwoProduct-exact in their hi * hi part, sums are Knuth TwoSum with the
+// rounding errors carried in a lo word, and every block finishes in FP64.
+// Pair terms (F != 0): a pair {y, y ^ F} contributes
+//   s_y * {2 Re w, -2 Im w, -2 Re w, 2 Im w}[nY mod 4],  w = conj(psi_{y^F}) psi_y,
+// (the y ^ F half equals the y half because popc(F & Q) = nY).  Diagonal
+// terms: a thread takes 16 amplitudes that differ in four local bits, forms
+// the Walsh-Hadamard transform W[u] = sum_j (-1)^popc(j & u) |psi_j|^2 of
+// those 16 and reads each term's contribution as +-W[QL restricted to the four
+// bits], so the per-term cost is paid once per 16 amplitudes.
 namespace {
-// Parse a Pauli sum into sweeps (one TermSet per distinct flip mask; identity
-// factors are dropped, an all-identity term is a diagonal term with Q = 0).
-int pauli_plan(int n, const qc_pauli_sum* H, std::vector<TermSet>& sets) {
+
+constexpr int kTileThreads = 256;
+constexpr int kTileMaxH = 8;       // generator masks per pass
+constexpr int kGroupTerms = 2;     // pair terms evaluated together per flip mask
+
+struct TTerm {                     // one term inside a pass
+  uint64_t q;                      // phase mask Q (global bit positions)
+  uint32_t ql;                     // local phase mask QL
+  uint32_t pad;
+  float kh, kl;                    // weight (c_t, times +-2 for pair terms) as hi + lo
+};
+struct TGroup {                    // pair terms sharing one local flip mask
+  uint32_t fl;                     // FL
+  int pivot;                       // highest set bit of FL
+  int t0, nt;                      // terms[t0 .. t0 + nt)
+  uint32_t kind;                   // bit 0: the terms weigh Im w (else Re w); bit 1: their
+                                   // local phase masks are nonzero (then nt <= kGroupTerms)
+};
+struct TPass {                     // kernel parameter: one pass
+  const TTerm* terms;
+  const TGroup* groups;
+  uint64_t ntiles;                 // 2^(n - L)
+  int m, h, L, wb;                 // low bits, generators, tile bits, WHT window
+  int ngroups, dt0, dnt;           // pair groups; diagonal terms [dt0, dt0 + dnt)
+  int piv[kTileMaxH];              // pivot bit of generator i, ascending in i
+  uint64_t gen[kTileMaxH];         // generator masks
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// (th, tl) += (kh + kl) * (vh + vl), hi * hi exact, the rest rounded once.
+__device__ __forceinline__ void acc_scaled(float& th, float& tl, float kh, float kl, float vh, float vl) {
+  const float p = __fmul_rn(kh, vh);
+  const float pe = __fmaf_rn(kh, vh, -p);
+  const float pl = __fmaf_rn(kh, vl, __fmaf_rn(kl, vh, pe));
+  float s, e;
+  two_sum(th, p, s, e);
+  th = s;
+  tl = __fadd_rn(tl, __fadd_rn(e, pl));
+}
+
+using P2 = ArC128p;                // packed FP32-pair instructions
+// -x per component on the FP32 pipe (0 - x; the sign of a zero does not matter here)
+__device__ __forceinline__ uint64_t neg2(uint64_t a) { return P2::sub2(0ull, a); }
+// (+-1, +-1) as a packed pair: -1 when `odd` has its lowest bit set
+__device__ __forceinline__ uint64_t sgn2(uint32_t odd) {
+  const uint32_t f = ((odd & 1u) << 31) | 0x3f800000u;
+  return (uint64_t)f | ((uint64_t)f << 32);
+}
+
+// Rounded product b * a per component, written as fma(b, a, z) with z a zero
+// the compiler cannot see (read from a kernel parameter): a plain multiply
+// that feeds the TwoSum below may be fused with its first add by the code
+// generator, and TwoSum is not error-free for such a fused sum.
+__device__ __forceinline__ uint64_t prod2(uint64_t b, uint64_t a, uint64_t z) { return P2::fma2(b, a, z); }
+
+// Packed TwoSum accumulation: (ah, al) += (p, e) per component.
+__device__ __forceinline__ void acc2(uint64_t& ah, uint64_t& al, uint64_t p, uint64_t e) {
+  const uint64_t t = P2::add2(ah, p);
+  const uint64_t z = P2::sub2(t, ah);
+  const uint64_t err = P2::add2(P2::sub2(ah, P2::sub2(t, z)), P2::sub2(p, z));
+  ah = t;
+  al = P2::add2(al, P2::add2(err, e));
+}
+
+// Tile entry: complex128 -> {hi pair (re, im), lo pair (re, im)} (16 bytes);
+// complex64 -> the amplitude itself (8 bytes; its lo pair is zero).
+template <bool C128> struct TileT;
+template <> struct TileT<true> {
+  static constexpr int E = 16;     // tile bytes per amplitude
+  static constexpr int G = 16;     // state bytes per amplitude
+  struct amp { uint64_t h, l; };
+  static __device__ __forceinline__ amp get(const unsigned char* t, uint32_t l) {
+    const uint4 v = *(const uint4*)(t + (size_t)l * 16);
+    return {(uint64_t)v.x | ((uint64_t)v.y << 32), (uint64_t)v.z | ((uint64_t)v.w << 32)};
+  }
+};
+template <> struct TileT<false> {
+  static constexpr int E = 8;
+  static constexpr int G = 8;
+  struct amp { uint64_t h, l; };
+  static __device__ __forceinline__ amp get(const unsigned char* t, uint32_t l) {
+    return {*(const uint64_t*)(t + (size_t)l * 8), 0ull};
+  }
+};
+
+// Load the tile with base index `base` into shared memory: 16-byte
+// asynchronous copies (cp.async, no registers held while they are in flight),
+// then each thread splits the complex128 entries it copied into hi + lo
+// floats in place.  A 16-byte chunk holds one complex128 or two complex64
+// amplitudes and never straddles a segment (segments are 2^m >= 2 amplitudes).
+template <bool C128>
+__device__ __forceinline__ void load_tile(const unsigned char* __restrict__ psi, uint64_t base,
+                                          const uint64_t* gtab, const TPass& P, unsigned char* tile) {
+  using T = TileT<C128>;
+  constexpr int CA = 16 / T::G;                       // amplitudes per chunk
+  const uint32_t nchunk = (1u << P.L) / CA;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile);
+  const uint32_t lowm = (1u << P.m) - 1u;
+  for (uint32_t v = threadIdx.x; v < nchunk; v += kTileThreads) {
+    const uint32_t l = v * CA;
+    const uint64_t y = (base ^ gtab[l >> P.m]) + (l & lowm);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"(sbase + v * 16u), "l"(psi + y * T::G) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if constexpr (C128) {
+    for (uint32_t v = threadIdx.x; v < nchunk; v += kTileThreads) {
+      uint4* d = (uint4*)(tile + (size_t)v * 16);
+      const uint4 x = *d;
+      const ArC128x::ff re = ArC128x::split(x.x, x.y);
+      const ArC128x::ff im = ArC128x::split(x.z, x.w);
+      *d = make_uint4(__float_as_uint(re.h), __float_as_uint(im.h), __float_as_uint(re.l), __float_as_uint(im.l));
+    }
+  }
+}
+
+// Pair terms of one group over the tile; adds their weighted sums to (th, tl).
+// IM: the group's terms weigh Im w (odd nY), else Re w.  SIGNED: the terms'
+// local phase masks are nonzero (at most kGroupTerms terms, one accumulator
+// each); otherwise every term of the group has the same in-tile sum and one
+// accumulator serves them all (any number of terms).
+template <bool C128, bool IM, bool SIGNED>
+__device__ __forceinline__ void tile_group(const unsigned char* tile, const TPass& P, const TGroup& g,
+                                           uint64_t base, uint64_t zz, float& th, float& tl) {
+  using T = TileT<C128>;
+  constexpr int NA = SIGNED ? kGroupTerms : 1;      // accumulators
+  uint32_t ql[NA];
+#pragma unroll
+  for (int k = 0; k < NA; k++) ql[k] = SIGNED ? __ldg(&P.terms[g.t0 + (k < g.nt ? k : 0)].ql) : 0u;
+  uint64_t ah[NA], al[NA];
+#pragma unroll
+  for (int k = 0; k < NA; k++) { ah[k] = 0ull; al[k] = 0ull; }
+  const uint32_t npairs = 1u << (P.L - 1);
+  const uint32_t hm = ~((1u << g.pivot) - 1u);     // l = j with a zero inserted at the pivot
+  // UNR pairs per iteration, their shared-memory loads issued first
+  constexpr int UNR = C128 ? 2 : 4;
+  const bool full = (npairs & (UNR * kTileThreads - 1)) == 0;
+  for (uint32_t j0 = threadIdx.x; j0 < npairs; j0 += UNR * kTileThreads) {
+    typename T::amp a[UNR], b[UNR];
+    uint32_t l[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; u++) {
+      uint32_t j = j0 + u * kTileThreads;
+      if (!full) j = min(j, npairs - 1u);
+      l[u] = j + (j & hm);
+      a[u] = T::get(tile, l[u]);
+      b[u] = T::get(tile, l[u] ^ g.fl);
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; u++) {
+      if (!full && j0 + u * kTileThreads >= npairs) break;
+      // w = conj(b) a:  Re w = br ar + bi ai (x + y of b*a),  Im w = br ai - bi ar
+      // (x - y of b * swap(a)).  Products: hi*hi exact, cross terms rounded.
+      const uint64_t ah_ = IM ? P2::swp(a[u].h) : a[u].h;
+      const uint64_t p = prod2(b[u].h, ah_, zz);
+      uint64_t e = P2::fma2(b[u].h, ah_, neg2(p));
+      if constexpr (C128) {
+        const uint64_t al_ = IM ? P2::swp(a[u].l) : a[u].l;
+        e = P2::add2(e, P2::fma2(b[u].h, al_, P2::mul2(b[u].l, ah_)));
+      }
+      if constexpr (SIGNED) {
+#pragma unroll
+        for (int k = 0; k < NA; k++) {
+          if (k < g.nt) {
+            const uint64_t sg = sgn2(__popc(l[u] & ql[k]));
+            acc2(ah[k], al[k], P2::mul2(p, sg), P2::mul2(e, sg));
+          }
+        }
+      } else {
+        acc2(ah[0], al[0], p, e);
+      }
+    }
+  }
+  // value = x + y (Re) or x - y (Im) of the packed sums
+  float vh[NA], vl[NA];
+#pragma unroll
+  for (int k = 0; k < NA; k++) {
+    const float hx = P2::lo32(ah[k]), lx = P2::lo32(al[k]);
+    const float hy = IM ? -P2::hi32(ah[k]) : P2::hi32(ah[k]);
+    const float ly = IM ? -P2::hi32(al[k]) : P2::hi32(al[k]);
+    float ve;
+    two_sum(hx, hy, vh[k], ve);
+    vl[k] = __fadd_rn(ve, __fadd_rn(lx, ly));
+  }
+  static_assert(kGroupTerms == 2, "the selects below pick one of two accumulators");
+  for (int k = 0; k < g.nt; k++) {
+    const TTerm* tt = &P.terms[g.t0 + k];
+    const float xh = (SIGNED && k == 1) ? vh[NA - 1] : vh[0];
+    const float xl = (SIGNED && k == 1) ? vl[NA - 1] : vl[0];
+    const bool neg = __popcll(base & __ldg(&tt->q)) & 1;
+    acc_scaled(th, tl, __ldg(&tt->kh), __ldg(&tt->kl), neg ? -xh : xh, neg ? -xl : xl);
+  }
+}
+
+// Diagonal terms over the tile (after the pair groups: overwrites the tile).
+template <bool C128>
+__device__ __forceinline__ void tile_diag(unsigned char* tile, const uint64_t* gtab, const TPass& P, uint64_t base,
+                                          uint64_t zz, float& th, float& tl) {
+  using T = TileT<C128>;
+  const uint32_t ntile = 1u << P.L;
+  const uint32_t nchunks = ntile >= 16 ? ntile >> 4 : 1u;
+  const int wb = P.wb;
+  for (uint32_t c = threadIdx.x; c < nchunks; c += kTileThreads) {
+    // chunk start: c deposited into the local bits outside [wb, wb + 4)
+    const uint32_t start = (c & ((1u << wb) - 1u)) | ((c >> wb) << (wb + 4));
+    float ph[16], pl[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const uint32_t l = start + ((uint32_t)k << wb);
+      ph[k] = 0.f;
+      pl[k] = 0.f;
+      if (l < ntile) {
+        const typename T::amp a = T::get(tile, l);
+        // |a|^2 = re^2 + im^2: hi*hi exact (TwoProduct), 2 hi*lo rounded
+        const uint64_t p = prod2(a.h, a.h, zz);
+        uint64_t e = P2::fma2(a.h, a.h, neg2(p));
+        if constexpr (C128) e = P2::add2(e, P2::mul2(P2::add2(a.h, a.h), a.l));
+        float s, r;
+        two_sum(P2::lo32(p), P2::hi32(p), s, r);
+        ph[k] = s;
+        pl[k] = __fadd_rn(r, __fadd_rn(P2::lo32(e), P2::hi32(e)));
+      }
+    }
+    // in-register Walsh-Hadamard transform over the 16 entries
+#pragma unroll
+    for (int b = 1; b < 16; b <<= 1) {
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        if (!(k & b)) {
+          const float xh = ph[k], xl = pl[k], yh = ph[k | b], yl = pl[k | b];
+          float s, e;
+          two_sum(xh, yh, s, e);
+          ph[k] = s;
+          pl[k] = __fadd_rn(__fadd_rn(xl, yl), e);
+          two_sum(xh, -yh, s, e);
+          ph[k | b] = s;
+          pl[k | b] = __fadd_rn(__fsub_rn(xl, yl), e);
+        }
+      }
+    }
+    // W[u] replaces entry u of the chunk (each thread reads back only its own)
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const uint32_t l = start + ((uint32_t)k << wb);
+      if (l < ntile || k == 0) *(float2*)(tile + (size_t)l * T::E) = make_float2(ph[k], pl[k]);
+    }
+    // global index of the chunk's first entry: base ^ G(hc) ^ low
+    const uint64_t y0 = base ^ gtab[start >> P.m] ^ (start & ((1u << P.m) - 1u));
+    constexpr int TU = 4;          // terms per iteration, their loads issued first
+    for (int t0 = P.dt0; t0 < P.dt0 + P.dnt; t0 += TU) {
+      uint32_t qlt[TU];
+      uint64_t qt[TU];
+      float kh[TU], kl[TU];
+#pragma unroll
+      for (int i = 0; i < TU; i++) {
+        const TTerm* tt = &P.terms[min(t0 + i, P.dt0 + P.dnt - 1)];
+        qlt[i] = __ldg(&tt->ql);
+        qt[i] = __ldg(&tt->q);
+        kh[i] = __ldg(&tt->kh);
+        kl[i] = __ldg(&tt->kl);
+      }
+      float2 w[TU];
+#pragma unroll
+      for (int i = 0; i < TU; i++) {
+        const uint32_t u = (qlt[i] >> wb) & 15u;
+        w[i] = *(const float2*)(tile + (size_t)(start + (u << wb)) * T::E);
+      }
+#pragma unroll
+      for (int i = 0; i < TU; i++) {
+        if (t0 + i < P.dt0 + P.dnt) {
+          // sign (-1)^popc(y0 & Q) of the chunk's first index y0, folded into the weight
+          const uint32_t sb = (uint32_t)__popcll(y0 & qt[i]) << 31;
+          acc_scaled(th, tl, __uint_as_float(__float_as_uint(kh[i]) ^ sb),
+                     __uint_as_float(__float_as_uint(kl[i]) ^ sb), w[i].x, w[i].y);
+        }
+      }
+    }
+  }
+}
+
+template <bool C128>
+__global__ void __launch_bounds__(kTileThreads, 3)
+k_pauli_tile(const unsigned char* __restrict__ psi, const __grid_constant__ TPass P, double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char tsm[];
+  using T = TileT<C128>;
+  unsigned char* tile = tsm;
+  uint64_t* gtab = (uint64_t*)(tsm + ((size_t)T::E << P.L));
+  for (int c = threadIdx.x; c < (1 << P.h); c += kTileThreads) {
+    uint64_t g = 0;
+    for (int i = 0; i < P.h; i++)
+      if ((c >> i) & 1) g ^= P.gen[i];
+    gtab[c] = g;
+  }
+  const uint64_t zz = P.ntiles >> 63;   // 0 (ntiles <= 2^36), opaque to the compiler
+  float th = 0.f, tl = 0.f;
+  for (uint64_t tix = blockIdx.x; tix < P.ntiles; tix += gridDim.x) {
+    uint64_t base = tix << P.m;
+    for (int i = 0; i < P.h; i++) base = qc_insert_zero(base, P.piv[i]);
+    __syncthreads();                 // previous tile consumed, gtab written
+    load_tile<C128>(psi, base, gtab, P, tile);
+    __syncthreads();
+    for (int gi = 0; gi < P.ngroups; gi++) {
+      TGroup g;
+      g.fl = __ldg(&P.groups[gi].fl);
+      g.pivot = __ldg(&P.groups[gi].pivot);
+      g.t0 = __ldg(&P.groups[gi].t0);
+      g.nt = __ldg(&P.groups[gi].nt);
+      g.kind = __ldg(&P.groups[gi].kind);
+      switch (g.kind) {
+        case 0: tile_group<C128, false, false>(tile, P, g, base, zz, th, tl); break;
+        case 1: tile_group<C128, true, false>(tile, P, g, base, zz, th, tl); break;
+        case 2: tile_group<C128, false, true>(tile, P, g, base, zz, th, tl); break;
+        default: tile_group<C128, true, true>(tile, P, g, base, zz, th, tl); break;
+      }
+    }
+    if (P.dnt > 0) {
+      __syncthreads();               // pair groups done reading the tile
+      tile_diag<C128>(tile, gtab, P, base, zz, th, tl);
+    }
+  }
+  const double tot = block_sum((double)th + (double)tl);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// ---- host planning --------------------------------------------------------
+struct HTerm { uint64_t F, Q; int ny; double c; };
+
+int parse_terms(int n, const qc_pauli_sum* H, std::vector<HTerm>& out) {
   if (!H || H->nterms < 0) return qc_fail(QC_ERR_ARG, "invalid Pauli sum");
   if (H->nterms > 0 && (!H->coeffs || !H->offsets)) return qc_fail(QC_ERR_ARG, "Pauli sum arrays are NULL");
-  std::map<uint64_t, size_t> by_flip;
+  out.clear();
   for (int t = 0; t < H->nterms; t++) {
     const int b = H->offsets[t], e = H->offsets[t + 1];
     if (e < b) return qc_fail(QC_ERR_ARG, "term %d: offsets decrease", t);
@@ -152,62 +517,294 @@ int pauli_plan(int n, const qc_pauli_sum* H, std::vector<TermSet>& sets) {
       else if (L == 'Z' || L == 'z') Q |= bit;
       else return qc_fail(QC_ERR_ARG, "term %d: unknown Pauli letter '%c'", t, L);
     }
-    const double c = H->coeffs[t];
-    auto it = by_flip.find(F);
-    if (it == by_flip.end() || sets[it->second].nterms == kMaxTermsPerSweep) {
-      TermSet ts;
-      std::memset(&ts, 0, sizeof(ts));
-      ts.flip = F;
-      ts.pivot = F ? 63 - __builtin_clzll(F) : -1;
-      by_flip[F] = sets.size();
-      sets.push_back(ts);
-      it = by_flip.find(F);
-    }
-    TermSet& ts = sets[it->second];
-    ts.phase_mask[ts.nterms] = Q;
-    ts.coeff[ts.nterms] = c;
-    ts.ipow[ts.nterms] = ny & 3;
-    ts.nterms++;
+    out.push_back({F, Q, ny, H->coeffs[t]});
   }
   return QC_OK;
 }
+
+// GF(2) basis in reduced form: every vector has its own pivot (highest set
+// bit) and no other vector has that bit set.
+struct Basis {
+  std::vector<uint64_t> v;
+  // Reduce x by the basis; hc gets bit i for every vector i used.
+  uint64_t reduce(uint64_t x, uint32_t* hc) const {
+    uint32_t c = 0;
+    for (size_t i = 0; i < v.size(); i++) {
+      const int p = 63 - __builtin_clzll(v[i]);
+      if ((x >> p) & 1ull) { x ^= v[i]; c |= 1u << i; }
+    }
+    if (hc) *hc = c;
+    return x;
+  }
+  // Add a reduced, nonzero vector.
+  void add(uint64_t r) {
+    const int p = 63 - __builtin_clzll(r);
+    for (auto& w : v)
+      if ((w >> p) & 1ull) w ^= r;
+    v.push_back(r);
+  }
+};
+
+struct HPass {
+  Basis basis;
+  std::vector<uint64_t> flips;     // distinct flip masks assigned here
+  double cost = 0.0;
+};
+
+struct TilePlan {
+  std::vector<TPass> passes;       // term/group pointers filled in at upload
+  std::vector<TTerm> terms;
+  std::vector<TGroup> groups;
+  std::vector<int> term_off, group_off;
+};
+
+double group_cost(uint64_t F, int nterms) {
+  return F == 0 ? 4.0 + 0.08 * nterms : 1.0 + 0.3 * nterms;
+}
+
+int tile_plan(int n, bool c128, const std::vector<HTerm>& terms_in, TilePlan& plan) {
+  // terms with the same flip and phase masks (hence the same nY) add up
+  std::vector<HTerm> terms;
+  {
+    std::map<std::pair<uint64_t, uint64_t>, size_t> seen;
+    for (const HTerm& t : terms_in) {
+      auto it = seen.find({t.F, t.Q});
+      if (it == seen.end()) {
+        seen[{t.F, t.Q}] = terms.size();
+        terms.push_back(t);
+      } else {
+        terms[it->second].c += t.c;
+      }
+    }
+  }
+  const int Lmax = c128 ? 12 : 13, mdef = c128 ? 5 : 6;
+  const int L = std::min(n, Lmax);
+  const int m = std::min(mdef, L);
+  const int h = L - m;
+  const uint64_t low = (1ull << m) - 1ull;
+  // distinct flip masks, in order of first appearance
+  std::vector<uint64_t> flips;
+  std::map<uint64_t, int> count;
+  for (const HTerm& t : terms) {
+    if (!count.count(t.F)) flips.push_back(t.F);
+    count[t.F]++;
+  }
+  std::vector<HPass> hp;
+  // masks with bits above the low ones: first pass whose span holds them, or
+  // that can still take one more generator
+  for (uint64_t F : flips) {
+    const uint64_t hi = F & ~low;
+    if (!hi) continue;
+    bool placed = false;
+    for (HPass& p : hp) {
+      const uint64_t r = p.basis.reduce(hi, nullptr);
+      if (r == 0 || (int)p.basis.v.size() < h) {
+        if (r) p.basis.add(r);
+        p.flips.push_back(F);
+        p.cost += group_cost(F, count[F]);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) {
+      hp.emplace_back();
+      hp.back().basis.add(hi);
+      hp.back().flips.push_back(F);
+      hp.back().cost += group_cost(F, count[F]);
+    }
+  }
+  if (hp.empty()) hp.emplace_back();
+  // masks within the low bits (and the diagonal terms) fit every pass: cheapest
+  for (uint64_t F : flips) {
+    if (F & ~low) continue;
+    HPass* best = &hp[0];
+    for (HPass& p : hp)
+      if (p.cost < best->cost) best = &p;
+    best->flips.push_back(F);
+    best->cost += group_cost(F, count[F]);
+  }
+  plan = TilePlan();
+  for (HPass& p : hp) {
+    // complete the basis with unit vectors at free bits above the low ones
+    // (a unit vector at a non-pivot bit reduces to itself)
+    for (int b = m; b < n && (int)p.basis.v.size() < h; b++) {
+      const uint64_t r = p.basis.reduce(1ull << b, nullptr);
+      if (r == (1ull << b)) p.basis.add(r);
+    }
+    if ((int)p.basis.v.size() != h) return qc_fail(QC_ERR_ARG, "internal: tile basis of rank %d, want %d",
+                                                  (int)p.basis.v.size(), h);
+    std::sort(p.basis.v.begin(), p.basis.v.end(),
+              [](uint64_t a, uint64_t b) { return __builtin_clzll(a) > __builtin_clzll(b); });
+    TPass P;
+    std::memset(&P, 0, sizeof(P));
+    P.ntiles = 1ull << (n - L);
+    P.m = m;
+    P.h = h;
+    P.L = L;
+    P.wb = L >= 8 ? 4 : 0;
+    for (int i = 0; i < h; i++) {
+      P.gen[i] = p.basis.v[i];
+      P.piv[i] = 63 - __builtin_clzll(p.basis.v[i]);
+    }
+    const int t_begin = (int)plan.terms.size(), g_begin = (int)plan.groups.size();
+    // local flip -> its terms (ordered for a deterministic layout)
+    std::map<uint32_t, std::vector<const HTerm*>> by_fl;
+    std::vector<const HTerm*> diag;
+    auto local_q = [&](uint64_t Q) {
+      uint32_t qh = 0;
+      for (int i = 0; i < h; i++) qh |= (uint32_t)(__builtin_popcountll(P.gen[i] & Q) & 1) << i;
+      return (qh << m) | (uint32_t)(Q & low);
+    };
+    std::vector<uint64_t> assigned(p.flips);
+    std::sort(assigned.begin(), assigned.end());
+    for (const HTerm& t : terms) {
+      if (!std::binary_search(assigned.begin(), assigned.end(), t.F)) continue;
+      if (t.F == 0) { diag.push_back(&t); continue; }
+      uint32_t hc = 0;
+      const uint64_t r = p.basis.reduce(t.F & ~low, &hc);
+      if (r) return qc_fail(QC_ERR_ARG, "internal: flip mask outside the pass span");
+      by_fl[(hc << m) | (uint32_t)(t.F & low)].push_back(&t);
+    }
+    static const double kw[4] = {2.0, -2.0, -2.0, 2.0};
+    auto push_term = [&](const HTerm* t, bool pair) {
+      TTerm x;
+      const double k = pair ? t->c * kw[t->ny & 3] : t->c;
+      x.q = t->Q;
+      x.ql = local_q(t->Q);
+      x.pad = 0u;
+      x.kh = (float)k;
+      x.kl = (float)(k - (double)x.kh);
+      plan.terms.push_back(x);
+    };
+    auto push_group = [&](uint32_t fl, uint32_t kind, const std::vector<const HTerm*>& v, size_t i0, size_t cnt) {
+      TGroup g;
+      g.fl = fl;
+      g.pivot = 31 - __builtin_clz(fl);
+      g.t0 = (int)plan.terms.size() - t_begin;
+      g.nt = (int)cnt;
+      g.kind = kind;
+      for (size_t k = 0; k < cnt; k++) push_term(v[i0 + k], true);
+      plan.groups.push_back(g);
+    };
+    for (auto& kv : by_fl) {
+      // split by Re / Im weight and by whether the phase mask reaches into the tile
+      std::vector<const HTerm*> part[4];
+      for (const HTerm* t : kv.second) part[(t->ny & 1) | (local_q(t->Q) ? 2 : 0)].push_back(t);
+      for (uint32_t kind = 0; kind < 4; kind++) {
+        const std::vector<const HTerm*>& v = part[kind];
+        if (v.empty()) continue;
+        if (kind & 2u) {
+          for (size_t i = 0; i < v.size(); i += kGroupTerms)
+            push_group(kv.first, kind, v, i, std::min<size_t>(kGroupTerms, v.size() - i));
+        } else {
+          push_group(kv.first, kind, v, 0, v.size());
+        }
+      }
+    }
+    P.dt0 = (int)plan.terms.size() - t_begin;
+    for (const HTerm* t : diag) push_term(t, false);
+    P.dnt = (int)diag.size();
+    P.ngroups = (int)plan.groups.size() - g_begin;
+    plan.term_off.push_back(t_begin);
+    plan.group_off.push_back(g_begin);
+    plan.passes.push_back(P);
+  }
+  return QC_OK;
+}
+
+// Grow-only device buffer per device for the term and group tables.
+std::map<int, std::pair<void*, size_t>> g_tables;
+
+int get_tables(int device, size_t bytes, void** p) {
+  auto& e = g_tables[device];
+  if (e.second < bytes) {
+    if (e.first) cudaFree(e.first);
+    e.first = nullptr;
+    e.second = 0;
+    cudaError_t err = cudaMalloc(&e.first, bytes);
+    if (err != cudaSuccess) { e.first = nullptr; return qc_cuda_fail(err, "cudaMalloc(term tables)"); }
+    e.second = bytes;
+  }
+  *p = e.first;
+  return QC_OK;
+}
+
+template <bool C128>
+int launch_tile(const qc_state* s, const TPass& P, double* partial, int grid) {
+  const size_t smem = ((size_t)TileT<C128>::E << P.L) + ((size_t)8 << P.h);
+  static bool attr[64] = {false};
+  const int dev = s->device;
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    QC_CUDA(cudaFuncSetAttribute(k_pauli_tile<C128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(((size_t)TileT<C128>::E << (C128 ? 12 : 13)) + (8 << kTileMaxH))));
+    QC_CUDA(cudaFuncSetAttribute(k_pauli_tile<C128>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    attr[dev] = true;
+  }
+  k_pauli_tile<C128><<<grid, kTileThreads, smem, s->stream>>>((const unsigned char*)s->ptr, P, partial);
+  QC_LAUNCHED("k_pauli_tile");
+  return QC_OK;
+}
+
 }  // namespace
+
+extern "C" int qc_expect_passes(int n, int dtype, const qc_pauli_sum* H, int* npasses) {
+  if (n < 1 || n > 36) return qc_fail(QC_ERR_ARG, "n=%d out of range 1..36", n);
+  if (dtype != QC_C64 && dtype != QC_C128) return qc_fail(QC_ERR_ARG, "unknown dtype %d", dtype);
+  if (!npasses) return qc_fail(QC_ERR_ARG, "npasses is NULL");
+  std::vector<HTerm> terms;
+  if (int rc = parse_terms(n, H, terms)) return rc;
+  if (terms.empty()) { *npasses = 0; return QC_OK; }
+  TilePlan plan;
+  if (int rc = tile_plan(n, dtype == QC_C128, terms, plan)) return rc;
+  *npasses = (int)plan.passes.size();
+  return QC_OK;
+}
 
 extern "C" int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out) {
   if (int rc = qc_check_state(s)) return rc;
   if (!out) return qc_fail(QC_ERR_ARG, "out is NULL");
-  std::vector<TermSet> sets;
-  if (int rc = pauli_plan(s->n, H, sets)) return rc;
+  std::vector<HTerm> terms;
+  if (int rc = parse_terms(s->n, H, terms)) return rc;
+  if (terms.empty()) { *out = 0.0; return QC_OK; }
+  const bool c128 = s->dtype != QC_C64;
+  TilePlan plan;
+  if (int rc = tile_plan(s->n, c128, terms, plan)) return rc;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  const uint64_t N = 1ull << s->n;
-  const int cap = qc_num_sms() * 8;
-  // grid per sweep and scratch layout: [partials of sweep 0 | sweep 1 | ...][result]
-  std::vector<int> grids(sets.size());
+  const int cap = qc_num_sms() * 3;
+  std::vector<int> grids(plan.passes.size());
   size_t total = 0;
-  for (size_t i = 0; i < sets.size(); i++) {
-    const uint64_t npairs = sets[i].pivot < 0 ? N : N / 2;
-    grids[i] = (int)std::max<uint64_t>(1, std::min<uint64_t>((npairs + kThreads - 1) / kThreads, cap));
+  for (size_t i = 0; i < plan.passes.size(); i++) {
+    grids[i] = (int)std::min<uint64_t>(plan.passes[i].ntiles, (uint64_t)cap);
     total += grids[i];
   }
   void* scratch = nullptr;
   if (int rc = get_scratch(s->device, (total + 1) * sizeof(double), &scratch)) return rc;
+  const size_t tbytes = plan.terms.size() * sizeof(TTerm);
+  const size_t gbytes = std::max<size_t>(1, plan.groups.size()) * sizeof(TGroup);
+  void* tables = nullptr;
+  if (int rc = get_tables(s->device, tbytes + gbytes, &tables)) return rc;
+  TTerm* dterms = (TTerm*)tables;
+  TGroup* dgroups = (TGroup*)((char*)tables + tbytes);
+  QC_CUDA(cudaMemcpyAsync(dterms, plan.terms.data(), tbytes, cudaMemcpyHostToDevice, s->stream));
+  if (!plan.groups.empty())
+    QC_CUDA(cudaMemcpyAsync(dgroups, plan.groups.data(), plan.groups.size() * sizeof(TGroup),
+                            cudaMemcpyHostToDevice, s->stream));
   double* partial = (double*)scratch;
   size_t off = 0;
-  for (size_t i = 0; i < sets.size(); i++) {
-    const uint64_t npairs = sets[i].pivot < 0 ? N : N / 2;
-    if (s->dtype == QC_C64)
-      k_pauli_sweep<float2><<<grids[i], kThreads, 0, s->stream>>>((const float2*)s->ptr, npairs, sets[i], partial + off);
-    else
-      k_pauli_sweep<double2><<<grids[i], kThreads, 0, s->stream>>>((const double2*)s->ptr, npairs, sets[i], partial + off);
-    QC_LAUNCHED("k_pauli_sweep");
+  for (size_t i = 0; i < plan.passes.size(); i++) {
+    TPass P = plan.passes[i];
+    P.terms = dterms + plan.term_off[i];
+    P.groups = dgroups + plan.group_off[i];
+    const int rc = c128 ? launch_tile<true>(s, P, partial + off, grids[i])
+                        : launch_tile<false>(s, P, partial + off, grids[i]);
+    if (rc) return rc;
     off += grids[i];
   }
   double result = 0.0;
-  if (total > 0) {
-    k_sum_partials<<<1, kThreads, 0, s->stream>>>(partial, (int)total, partial + total);
-    QC_LAUNCHED("k_sum_partials");
-    QC_CUDA(cudaMemcpyAsync(&result, partial + total, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  }
+  k_sum_partials<<<1, kThreads, 0, s->stream>>>(partial, (int)total, partial + total);
+  QC_LAUNCHED("k_sum_partials");
+  QC_CUDA(cudaMemcpyAsync(&result, partial + total, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   QC_CUDA(cudaStreamSynchronize(s->stream));
   *out = result;
   return QC_OK;

@@ -102,6 +102,7 @@ def _load():
         "qc_apply_circuit": [P, ctypes.POINTER(qc_gate), I, ctypes.POINTER(qc_opts)],
         "qc_expect": [P, ctypes.POINTER(qc_pauli_sum), DP],
         "qc_expect_noalloc": [P, ctypes.POINTER(qc_pauli_sum), DP],
+        "qc_expect_passes": [I, I, ctypes.POINTER(qc_pauli_sum), IP],
         "qc_fuse_plan": [I, ctypes.POINTER(qc_gate), I, I, ctypes.POINTER(qc_block), I, IP],
         "qc_adjoint_grad": [I, ctypes.POINTER(qc_gate), I, DP, I, ctypes.POINTER(qc_pauli_sum), DP, DP,
                             ctypes.POINTER(qc_grad_opts)],
@@ -325,6 +326,15 @@ class State:
         _check(lib.qc_expect_noalloc(self._h, ctypes.byref(rec), ctypes.byref(out)))
         del keep
         return out.value
+
+
+def expect_passes(n: int, dtype: int, hamiltonian) -> int:
+    """Host-only: how many passes over the state qc_expect makes for H."""
+    rec, keep = pauli_record(hamiltonian)
+    out = ctypes.c_int(0)
+    _check(lib.qc_expect_passes(n, dtype, ctypes.byref(rec), ctypes.byref(out)))
+    del keep
+    return out.value
 
 
 def fuse_plan(n: int, gates, fuse_k: int):
