@@ -321,13 +321,24 @@ __device__ __forceinline__ void tile_group(const unsigned char* tile, const TPas
       // w = conj(b) a:  Re w = br ar + bi ai (x + y of b*a),  Im w = br ai - bi ar
       // (x - y of b * swap(a)).  Products: hi*hi exact, cross terms rounded.
       const uint64_t ah_ = IM ? P2::swp(a[u].h) : a[u].h;
-      const uint64_t p = prod2(b[u].h, ah_, zz);
-      uint64_t e = P2::fma2(b[u].h, ah_, neg2(p));
+      uint64_t p = 0, e = 0;
       if constexpr (C128) {
+        p = prod2(b[u].h, ah_, zz);
+        e = P2::fma2(b[u].h, ah_, neg2(p));
         const uint64_t al_ = IM ? P2::swp(a[u].l) : a[u].l;
         e = P2::add2(e, P2::fma2(b[u].h, al_, P2::mul2(b[u].l, ah_)));
       }
-      if constexpr (SIGNED) {
+      if constexpr (!C128) {
+        // complex64: FP32 products and in-tile partial sums (one packed fma per
+        // pair and term); the sums across tiles stay float-float
+        if constexpr (SIGNED) {
+#pragma unroll
+          for (int k = 0; k < NA; k++)
+            if (k < g.nt) ah[k] = P2::fma2(P2::mul2(b[u].h, sgn2(__popc(l[u] & ql[k]))), ah_, ah[k]);
+        } else {
+          ah[0] = P2::fma2(b[u].h, ah_, ah[0]);
+        }
+      } else if constexpr (SIGNED) {
 #pragma unroll
         for (int k = 0; k < NA; k++) {
           if (k < g.nt) {
@@ -380,14 +391,18 @@ __device__ __forceinline__ void tile_diag(unsigned char* tile, const uint64_t* g
       pl[k] = 0.f;
       if (l < ntile) {
         const typename T::amp a = T::get(tile, l);
-        // |a|^2 = re^2 + im^2: hi*hi exact (TwoProduct), 2 hi*lo rounded
         const uint64_t p = prod2(a.h, a.h, zz);
-        uint64_t e = P2::fma2(a.h, a.h, neg2(p));
-        if constexpr (C128) e = P2::add2(e, P2::mul2(P2::add2(a.h, a.h), a.l));
-        float s, r;
-        two_sum(P2::lo32(p), P2::hi32(p), s, r);
-        ph[k] = s;
-        pl[k] = __fadd_rn(r, __fadd_rn(P2::lo32(e), P2::hi32(e)));
+        if constexpr (C128) {
+          // |a|^2 = re^2 + im^2: hi*hi exact (TwoProduct), 2 hi*lo rounded
+          uint64_t e = P2::fma2(a.h, a.h, neg2(p));
+          e = P2::add2(e, P2::mul2(P2::add2(a.h, a.h), a.l));
+          float s, r;
+          two_sum(P2::lo32(p), P2::hi32(p), s, r);
+          ph[k] = s;
+          pl[k] = __fadd_rn(r, __fadd_rn(P2::lo32(e), P2::hi32(e)));
+        } else {
+          ph[k] = __fadd_rn(P2::lo32(p), P2::hi32(p));     // complex64: FP32
+        }
       }
     }
     // in-register Walsh-Hadamard transform over the 16 entries
@@ -397,13 +412,18 @@ __device__ __forceinline__ void tile_diag(unsigned char* tile, const uint64_t* g
       for (int k = 0; k < 16; k++) {
         if (!(k & b)) {
           const float xh = ph[k], xl = pl[k], yh = ph[k | b], yl = pl[k | b];
-          float s, e;
-          two_sum(xh, yh, s, e);
-          ph[k] = s;
-          pl[k] = __fadd_rn(__fadd_rn(xl, yl), e);
-          two_sum(xh, -yh, s, e);
-          ph[k | b] = s;
-          pl[k | b] = __fadd_rn(__fsub_rn(xl, yl), e);
+          if constexpr (C128) {
+            float s, e;
+            two_sum(xh, yh, s, e);
+            ph[k] = s;
+            pl[k] = __fadd_rn(__fadd_rn(xl, yl), e);
+            two_sum(xh, -yh, s, e);
+            ph[k | b] = s;
+            pl[k | b] = __fadd_rn(__fsub_rn(xl, yl), e);
+          } else {
+            ph[k] = __fadd_rn(xh, yh);
+            ph[k | b] = __fsub_rn(xh, yh);
+          }
         }
       }
     }
@@ -416,6 +436,7 @@ __device__ __forceinline__ void tile_diag(unsigned char* tile, const uint64_t* g
     // global index of the chunk's first entry: base ^ G(hc) ^ low
     const uint64_t y0 = base ^ gtab[start >> P.m] ^ (start & ((1u << P.m) - 1u));
     constexpr int TU = 4;          // terms per iteration, their loads issued first
+    float dsum = 0.f;              // complex64: the chunk's terms, summed in FP32
     for (int t0 = P.dt0; t0 < P.dt0 + P.dnt; t0 += TU) {
       uint32_t qlt[TU];
       uint64_t qt[TU];
@@ -439,10 +460,19 @@ __device__ __forceinline__ void tile_diag(unsigned char* tile, const uint64_t* g
         if (t0 + i < P.dt0 + P.dnt) {
           // sign (-1)^popc(y0 & Q) of the chunk's first index y0, folded into the weight
           const uint32_t sb = (uint32_t)__popcll(y0 & qt[i]) << 31;
-          acc_scaled(th, tl, __uint_as_float(__float_as_uint(kh[i]) ^ sb),
-                     __uint_as_float(__float_as_uint(kl[i]) ^ sb), w[i].x, w[i].y);
+          if constexpr (C128)
+            acc_scaled(th, tl, __uint_as_float(__float_as_uint(kh[i]) ^ sb),
+                       __uint_as_float(__float_as_uint(kl[i]) ^ sb), w[i].x, w[i].y);
+          else
+            dsum = __fmaf_rn(__uint_as_float(__float_as_uint(kh[i]) ^ sb), w[i].x, dsum);
         }
       }
+    }
+    if constexpr (!C128) {           // the chunk's FP32 sum joins the float-float total
+      float s, e;
+      two_sum(th, dsum, s, e);
+      th = s;
+      tl = __fadd_rn(tl, e);
     }
   }
 }

@@ -12,7 +12,11 @@ factorises into single-qubit Bloch components.
 
 Tolerance: complex128 1e-12 absolute on sums of O(1) coefficients (the
 float-float arithmetic carries 47-bit amplitudes and exact hi*hi products);
-complex64 1e-6 against the oracle evaluated on the same (complex64) amplitudes.
+complex64 2e-6 * max(1, sum |c_t|) against the oracle evaluated on the same
+(complex64) amplitudes: complex64 products and each thread's in-tile partial
+sums (at most 16 products) are FP32, the sums across tiles float-float, so
+the error is bounded by about 16 * 2^-24 of sum |c_t| -- two orders of
+magnitude inside the 2e-4 stated for complex64 energies.
 """
 import math
 
@@ -25,7 +29,11 @@ from paper_2303_00123_gb300.circuits import Gate
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"c128": 1e-12, "c64": 1e-6}
+TOL = {"c128": 1e-12, "c64": 2e-6}
+
+
+def tol(dtype, H):
+    return TOL[dtype] * (1.0 if dtype == "c128" else max(1.0, sum(abs(c) for c, _ in H)))
 
 
 @pytest.fixture(scope="module")
@@ -58,7 +66,7 @@ def check(q, n, dtype, H, seed=5):
     ref = O.expect(ref_psi, n, H)
     got = st.expect(H)
     st.free()
-    assert abs(got - ref) <= TOL[dtype], (n, dtype, got, ref)
+    assert abs(got - ref) <= tol(dtype, H), (n, dtype, got, ref)
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
