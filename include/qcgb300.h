@@ -201,7 +201,13 @@ int qc_apply_circuit(qc_state* s, const qc_gate* gates, int ngates, const qc_opt
  * commuting phase gates that all involve qubit `anchor` (for instance the
  * controlled phases of one QFT stage, Fig. 1), applied in one sweep:
  * amplitudes whose anchor bit is 1 are multiplied by
- * exp(i (theta0 + sum_j bit(lin_qubits[j]) * lin_theta[j])). */
+ * exp(i (theta0 + sum_j bit(lin_qubits[j]) * lin_theta[j])).  A kind-1 block
+ * with k = 1 first applies the 2x2 matrix U to qubits[0] == anchor in the same
+ * sweep: a lone 1-qubit gate on the anchor right before the run (the Hadamard
+ * of a QFT stage) joins it when the anchor's stride is at least 16
+ * amplitudes (qubit index <= n - 5).  kind 2: a run of two or more SWAP
+ * gates on disjoint qubit pairs (the final swaps of the QFT, Fig. 1) applied
+ * as one sweep that permutes the index bits. */
 #define QC_MAX_LIN 36
 typedef struct {
   int k;
@@ -210,7 +216,10 @@ typedef struct {
   int controls[QC_MAX_CONTROLS];
   int cstates[QC_MAX_CONTROLS];
   double U[2 * 32 * 32];            /* 2^k x 2^k complex, row-major (re, im) */
-  int kind;                         /* 0: matrix block, 1: linear phase run */
+  int kind;                         /* 0: matrix block, 1: linear phase run,
+                                       2: SWAPs on disjoint qubit pairs
+                                       (lin_qubits[2j], lin_qubits[2j+1]),
+                                       j < nlin / 2, as one bit permutation */
   int anchor;
   int nlin;
   int lin_qubits[QC_MAX_LIN];

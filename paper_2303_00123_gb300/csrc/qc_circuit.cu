@@ -272,6 +272,16 @@ bool phase_gate(const Resolved& R, int* qs, int* nq, double* theta) {
   return true;
 }
 
+// An uncontrolled SWAP: the 4x4 permutation exchanging |01> and |10>.
+bool swap_gate(const Resolved& R) {
+  if (R.k != 2 || R.nc != 0) return false;
+  static const int perm[4] = {0, 2, 1, 3};
+  for (int r = 0; r < 4; r++)
+    for (int c = 0; c < 4; c++)
+      if (R.U[r * 4 + c] != cd(c == perm[r] ? 1.0 : 0.0)) return false;
+  return true;
+}
+
 void emit_matrix_segment(int n, const std::vector<Resolved>& res, int begin, int end, int fuse_k,
                          std::vector<qc_op>& ops) {
   if (begin >= end) return;
@@ -334,6 +344,30 @@ int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc
           j++;
         }
       }
+      // longest run of SWAPs on disjoint qubit pairs from i: one bit permutation
+      int js = i;
+      uint64_t used = 0;
+      while (phase_runs && js < ngates && swap_gate(res[js])) {
+        const uint64_t pr = (1ull << res[js].t[0]) | (1ull << res[js].t[1]);
+        if (used & pr) break;
+        used |= pr;
+        js++;
+      }
+      if (js - i >= 2) {
+        emit_matrix_segment(n, res, seg_begin, i, fuse_k, ops);
+        qc_op op;
+        std::memset(&op, 0, sizeof(op));
+        op.kind = QC_OP_PERMUTE;
+        for (int g = i; g < js; g++) {
+          op.perm_a[op.nperm] = n - 1 - res[g].t[0];
+          op.perm_b[op.nperm] = n - 1 - res[g].t[1];
+          op.nperm++;
+        }
+        ops.push_back(op);
+        i = js;
+        seg_begin = js;
+        continue;
+      }
       if (j - i >= 2) {
         emit_matrix_segment(n, res, seg_begin, i, fuse_k, ops);
         const int anchor = __builtin_ctzll(common);   // a qubit shared by every gate of the run
@@ -352,6 +386,19 @@ int plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc
         }
         for (int q = 0; q < n; q++)
           if ((linmask >> q) & 1) { op.lin_pos[op.nlin] = n - 1 - q; op.lin_theta[op.nlin] = lin[q]; op.nlin++; }
+        // A lone 1-qubit op on the anchor just before the run (the H of a QFT
+        // stage, Fig. 1) joins the run's sweep: U on the anchor pair, then the
+        // phase.  The merged kernel needs the anchor at bit 4 or above.
+        if (!ops.empty() && op.anchor >= 4) {
+          const qc_op& last = ops.back();
+          if (last.kind == QC_OP_MATRIX && last.k == 1 && last.nc == 0 && last.tpos[0] == op.anchor) {
+            op.pre = 1;
+            op.k = 1;
+            op.tpos[0] = op.anchor;
+            std::memcpy(op.U, last.U, sizeof(double) * 8);
+            ops.pop_back();
+          }
+        }
         ops.push_back(op);
         i = j;
         seg_begin = j;
@@ -381,12 +428,26 @@ extern "C" int qc_fuse_plan(int n, const qc_gate* gates, int ngates, int fuse_k,
     const qc_op& op = ops[i];
     qc_block& b = blocks[i];
     std::memset(&b, 0, sizeof(b));
+    if (op.kind == QC_OP_PERMUTE) {   // pairs of qubits in lin_qubits
+      b.kind = 2;
+      b.nlin = 2 * op.nperm;
+      for (int j = 0; j < op.nperm; j++) {
+        b.lin_qubits[2 * j] = n - 1 - op.perm_a[j];
+        b.lin_qubits[2 * j + 1] = n - 1 - op.perm_b[j];
+      }
+      continue;
+    }
     if (op.kind == QC_OP_LINEAR_PHASE) {
       b.kind = 1;
       b.anchor = n - 1 - op.anchor;
       b.nlin = op.nlin;
       for (int j = 0; j < op.nlin; j++) { b.lin_qubits[j] = n - 1 - op.lin_pos[j]; b.lin_theta[j] = op.lin_theta[j]; }
       b.theta0 = op.theta0;
+      if (op.pre) {                  // the 2x2 matrix on the anchor applied first
+        b.k = 1;
+        b.qubits[0] = b.anchor;
+        std::memcpy(b.U, op.U, sizeof(double) * 8);
+      }
       continue;
     }
     b.k = op.k;

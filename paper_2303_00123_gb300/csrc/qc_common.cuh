@@ -370,7 +370,7 @@ struct ArC128p {
 // --------------------------------------------------------------------------
 enum qc_struct { QC_ST_DENSE = 0, QC_ST_PERM = 1, QC_ST_PHASE = 2 };
 
-enum qc_op_kind { QC_OP_MATRIX = 0, QC_OP_LINEAR_PHASE = 1 };
+enum qc_op_kind { QC_OP_MATRIX = 0, QC_OP_LINEAR_PHASE = 1, QC_OP_PERMUTE = 2 };
 
 struct qc_op {
   int kind;                     // qc_op_kind
@@ -388,6 +388,13 @@ struct qc_op {
   int lin_pos[QC_MAX_LIN];
   double lin_theta[QC_MAX_LIN];
   double theta0;
+  // QC_OP_LINEAR_PHASE with pre = 1: the 2x2 matrix U on the anchor (k = 1,
+  // tpos[0] = anchor) is applied first, in the same sweep.
+  int pre;
+  // QC_OP_PERMUTE: a run of SWAP gates on disjoint qubit pairs, i.e. the bit
+  // positions perm_a[i] and perm_b[i] of every basis index trade values.
+  int nperm;
+  int perm_a[18], perm_b[18];
 };
 
 // Resolve a gate record (named or explicit matrix) into an op: validates the
@@ -399,7 +406,8 @@ int qc_tc_timeouts(int* count);
 
 // Launch plan of a circuit: one op per gate, or per fused block (fuse_k >= 2);
 // with phase_runs, runs of commuting phase gates sharing a qubit become one
-// QC_OP_LINEAR_PHASE op.
+// QC_OP_LINEAR_PHASE op (taking along a 1-qubit op on the anchor just before
+// the run) and runs of SWAPs on disjoint pairs one QC_OP_PERMUTE op.
 #include <vector>
 int qc_plan_ops(int n, const qc_gate* gates, int ngates, int fuse_k, std::vector<qc_op>& ops,
                 bool phase_runs = false);

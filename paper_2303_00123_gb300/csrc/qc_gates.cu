@@ -21,6 +21,7 @@
 //   k_kq     -- dense k-qubit gate, k <= 5, any placement (Sec. 2.4; used for
 //               fused blocks and for very small states)
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -597,6 +598,279 @@ k_linear_phase(vec32* __restrict__ st, const __grid_constant__ LinGeom lg, const
   }
 }
 
+// ---------------------------------------------------------------- dense 1q + linear phase
+// One sweep for a 1-qubit gate U on the anchor followed by a run of phase
+// gates that all involve the anchor (Sec. 2.2-2.4 gates, merged): every pair
+// (a0, a1) of the anchor becomes U (a0, a1), then its anchor-1 member is
+// multiplied by exp(i phi(y)), phi(y) = theta0 + sum_j theta_j y_{lin_j}
+// (equal for both members: the linear qubits exclude the anchor).  A thread
+// takes R consecutive pairs of vectors.  The factor of the linear bits above
+// its window (the L in-vector bits and the log2 R bits that index the run) is
+// formed once per run from tables of <= 8 bits; the window's factor comes from
+// a table of V * R entries.  The high tables use the arithmetic HiAr<Ar> (the
+// scalar float-float form for the packed policy, whose coefficients are three
+// times larger), converted to a coefficient of Ar once per run.
+template <class Ar> struct HiAr { using type = Ar; };
+template <> struct HiAr<ArC128p> { using type = ArC128x; };
+
+template <class Ar> struct PhaseCoef;
+template <> struct PhaseCoef<ArC64> {
+  static __device__ __forceinline__ ArC64::val_t one() { return {1.f, 0.f}; }
+  static __device__ __forceinline__ ArC64::coef_t of(const ArC64::val_t& v) { return {v.re, v.im}; }
+};
+template <> struct PhaseCoef<ArC128> {
+  static __device__ __forceinline__ ArC128::val_t one() { return {1.0, 0.0}; }
+  static __device__ __forceinline__ ArC128::coef_t of(const ArC128::val_t& v) { return {v.re, v.im}; }
+};
+template <> struct PhaseCoef<ArC128x> {
+  static __device__ __forceinline__ ArC128x::val_t one() { return {{1.f, 0.f}, {0.f, 0.f}}; }
+  static __device__ __forceinline__ ArC128x::coef_t of(const ArC128x::val_t& v) {
+    return {v.re.h, v.re.l, v.im.h, v.im.l};
+  }
+};
+template <> struct PhaseCoef<ArC128p> {
+  static __device__ __forceinline__ ArC128x::val_t one() { return PhaseCoef<ArC128x>::one(); }
+  static __device__ __forceinline__ ArC128p::coef_t of(const ArC128x::val_t& v) {
+    const float rh = v.re.h, rl = v.re.l, ih = v.im.h, il = v.im.l;
+    ArC128p::coef_t c;
+    c.ah = ArC128p::pk(rh, rh); c.al = ArC128p::pk(rl, rl); c.anh = ArC128p::pk(-rh, -rh);
+    c.bh = ArC128p::pk(-ih, ih); c.bl = ArC128p::pk(-il, il); c.bnh = ArC128p::pk(ih, -ih);
+    return c;
+  }
+};
+
+constexpr int kDlGroups = 5;                 // high tables (36 linear bits, 8 per table)
+constexpr int kDlHiTab = kDlGroups * 256;
+constexpr int kDlR = 4;                      // vector pairs per thread and run
+
+struct DLGeom {
+  Geom g;                                    // pairs of vectors split by the anchor
+  int nhg;                                   // high tables
+  int hbits[kDlGroups];
+  int hcontig[kDlGroups];
+  int hpos[kDlGroups][8];                    // amplitude-index bit positions, lowest first
+  int hoff[kDlGroups];                       // first entry of each table
+};
+
+template <class Ar>
+struct DLTab {
+  typename HiAr<Ar>::type::coef_t hi[kDlHiTab];
+  typename Ar::coef_t w[Ar::V * kDlR];
+};
+
+template <class Ar, int R>
+__global__ void __launch_bounds__(kThreads, 2)
+k_dense_linphase(vec32* __restrict__ st, const __grid_constant__ DLGeom dg, const __grid_constant__ MatD<Ar, 2> M,
+                 const __grid_constant__ DLTab<Ar> tab, int nhi) {
+  constexpr int V = Ar::V;
+  constexpr int L = V == 4 ? 2 : 1;
+  using Hi = typename HiAr<Ar>::type;
+  using val_t = typename Ar::val_t;
+  __shared__ typename Hi::coef_t Th[kDlHiTab];
+  __shared__ typename Ar::coef_t Tw[V * R];
+  for (int i = threadIdx.x; i < nhi; i += kThreads) Th[i] = tab.hi[i];
+  for (int i = threadIdx.x; i < V * R; i += kThreads) Tw[i] = tab.w[i];
+  __syncthreads();
+  const uint64_t nruns = dg.g.ntiles / R;
+  const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+  for (uint64_t jr = (uint64_t)blockIdx.x * kThreads + threadIdx.x; jr < nruns; jr += stride) {
+    uint64_t vi[2];
+    tile_vectors<1>(dg.g, tile_base(dg.g, jr * R), vi);   // vi[0]: anchor 0, vi[1]: anchor 1
+    vec32 r0[R], r1[R];
+#pragma unroll
+    for (int k = 0; k < R; k++) { r0[k] = qc_ld32(st + vi[0] + k); r1[k] = qc_ld32(st + vi[1] + k); }
+    // factor of the linear bits above the window: the same for the whole run
+    const uint64_t y = vi[1] << L;
+    typename Hi::val_t h = PhaseCoef<Ar>::one();
+    for (int gi = 0; gi < dg.nhg; gi++) {
+      uint32_t m;
+      if (dg.hcontig[gi]) {
+        m = (uint32_t)(y >> dg.hpos[gi][0]) & ((1u << dg.hbits[gi]) - 1u);
+      } else {
+        m = 0;
+        for (int b = 0; b < dg.hbits[gi]; b++) m |= (uint32_t)((y >> dg.hpos[gi][b]) & 1u) << b;
+      }
+      h = Hi::template dot<1>(&Th[dg.hoff[gi] + m], &h);
+    }
+    const typename Ar::coef_t hc = PhaseCoef<Ar>::of(h);
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+#pragma unroll
+      for (int e = 0; e < V; e++) {
+        val_t in[2] = {Ar::load(r0[k], e), Ar::load(r1[k], e)};
+        const val_t o0 = Ar::template dot<2>(&M.m[0], in);
+        val_t o1 = Ar::template dot<2>(&M.m[2], in);
+        o1 = Ar::template dot<1>(&hc, &o1);
+        o1 = Ar::template dot<1>(&Tw[k * V + e], &o1);
+        Ar::store(r0[k], e, o0);
+        Ar::store(r1[k], e, o1);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < R; k++) { qc_st32(st + vi[0] + k, r0[k]); qc_st32(st + vi[1] + k, r1[k]); }
+  }
+}
+
+// ---------------------------------------------------------------- bit permutation
+// A run of SWAP gates on disjoint qubit pairs (Sec. 2.3's SWAP, merged): the
+// bit permutation pi swaps the paired bit positions of every basis index and
+// is its own inverse.  Tile bits T = [0, t) + pi([0, t)): pi maps T onto T,
+// so a tile (fixed values of the bits outside T) lands on the tile whose
+// outside bits are permuted by pi; a CTA takes such a pair of tiles (or one
+// tile mapped onto itself), reads both and writes both, so the update is in
+// place.  Reads and writes both run over segments of 2^t contiguous
+// amplitudes; the gather between them goes through shared memory, guided by
+// a table src[u] = local index (in the source tile) of output local index u.
+constexpr int kPermT = 5;                     // low tile bits: segments of 2^5 amplitudes
+constexpr int kPermMaxTile = 1 << (2 * kPermT); // amplitudes per tile (t low bits + <= t more)
+constexpr int kPermBatch = kThreads;          // tile pairs resolved per batch
+
+struct PermGeom {
+  int t, h;                                   // low bits, high tile bits
+  int hpos[kPermT];                           // high tile bit positions (ascending)
+  int nins;                                   // tile bit positions, ascending (for the deposit)
+  int ins[2 * kPermT];
+  int npairs;                                 // pairs of outside bits, as indices of the compressed tile number
+  int pa[18], pb[18];
+  uint64_t ntiles;
+};
+struct PermTab { uint16_t src[kPermMaxTile]; };
+
+// Shared-memory slot of tile entry l: the segment number (l >> t) XORed into
+// the 16-byte bank group, so that the gather, which reads entries of
+// different segments at equal offsets (a transpose, for the bit reversal),
+// and the segment-wise copies are both free of bank conflicts.  complex64
+// keeps entry pairs (one 16-byte chunk) together.
+template <int E>
+__device__ __forceinline__ uint32_t perm_slot(uint32_t l, int t) {
+  constexpr int S = E == 16 ? 0 : 1;
+  return l ^ (((l >> t) & 7u) << S);
+}
+
+// Copies of one tile into shared memory: 16-byte cp.async chunks (a chunk
+// holds 16 / E amplitudes and never straddles a 2^t segment).
+template <int E>
+__device__ __forceinline__ void perm_issue(const unsigned char* __restrict__ st, uint64_t f, const uint64_t* hdep,
+                                           uint32_t ntile, int t, uint32_t sdst) {
+  constexpr int CA = 16 / E;
+  const uint32_t lowm = (1u << t) - 1u;
+  for (uint32_t c = threadIdx.x; c < ntile / CA; c += kThreads) {
+    const uint32_t u = c * CA;
+    const uint64_t y = f | hdep[u >> t] | (u & lowm);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"(sdst + perm_slot<E>(u, t) * (uint32_t)E), "l"(st + y * E) : "memory");
+  }
+}
+
+template <int E>
+__global__ void __launch_bounds__(kThreads)
+k_permute(vec32* __restrict__ st, const __grid_constant__ PermGeom pg, const __grid_constant__ PermTab tab) {
+  constexpr int VA = 32 / E;                  // amplitudes per 32-byte vector
+  constexpr int W = E / 4;                    // words per amplitude
+  extern __shared__ __align__(16) unsigned char psm[];
+  const uint32_t ntile = 1u << (pg.t + pg.h);
+  // two stages, each holding a tile and its partner
+  uint32_t* buf = (uint32_t*)psm;             // [stage][A|B][ntile * W]
+  uint16_t* src = (uint16_t*)(buf + 4 * ntile * W);
+  uint64_t* hdep = (uint64_t*)(((uintptr_t)(src + ntile) + 7) & ~(uintptr_t)7);
+  uint64_t* s_in = hdep + (1 << pg.h);
+  uint64_t* s_out = s_in + kPermBatch;
+  int* s_list = (int*)(s_out + kPermBatch);   // canonical pairs of the batch
+  int* s_cnt = s_list + kPermBatch;
+  for (uint32_t i = threadIdx.x; i < ntile; i += kThreads) src[i] = tab.src[i];
+  for (int c = threadIdx.x; c < (1 << pg.h); c += kThreads) {
+    uint64_t d = 0;
+    for (int i = 0; i < pg.h; i++) d |= (uint64_t)((c >> i) & 1) << pg.hpos[i];
+    hdep[c] = d;
+  }
+  const unsigned char* stb = (const unsigned char*)st;
+  const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(buf);
+  const uint32_t tbytes = ntile * E;
+  const uint32_t nvec = ntile / VA;
+  const uint32_t lowm = (1u << pg.t) - 1u;
+  for (uint64_t b0 = (uint64_t)blockIdx.x * kPermBatch; b0 < pg.ntiles; b0 += (uint64_t)gridDim.x * kPermBatch) {
+    __syncthreads();
+    {
+      // tile number -> its partner, and both as fixed (outside-T) index bits
+      const uint64_t tau = b0 + threadIdx.x;
+      uint64_t tp = tau;
+      for (int i = 0; i < pg.npairs; i++) {
+        const uint64_t d = ((tp >> pg.pa[i]) ^ (tp >> pg.pb[i])) & 1ull;
+        tp ^= (d << pg.pa[i]) | (d << pg.pb[i]);
+      }
+      uint64_t fi = tau, fo = tp;
+      for (int i = 0; i < pg.nins; i++) { fi = qc_insert_zero(fi, pg.ins[i]); fo = qc_insert_zero(fo, pg.ins[i]); }
+      s_in[threadIdx.x] = fi;
+      s_out[threadIdx.x] = fo;
+      const bool ok = tau < pg.ntiles && tau <= tp;
+      // compact the canonical pairs of the batch (in tile order)
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      __shared__ int wcount[kThreads / 32];
+      if ((threadIdx.x & 31) == 0) wcount[threadIdx.x >> 5] = __popc(m);
+      __syncthreads();
+      int base = 0;
+      for (int w = 0; w < (int)(threadIdx.x >> 5); w++) base += wcount[w];
+      if (ok) s_list[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = threadIdx.x;
+      if (threadIdx.x == kThreads - 1) *s_cnt = base + __popc(m);
+    }
+    __syncthreads();
+    const int cnt = *s_cnt;
+    // pipeline: the copies of pair k + 1 are in flight while pair k is written
+    if (cnt > 0) {
+      const int i0 = s_list[0];
+      perm_issue<E>(stb, s_in[i0], hdep, ntile, pg.t, sbuf);
+      if (s_in[i0] != s_out[i0]) perm_issue<E>(stb, s_out[i0], hdep, ntile, pg.t, sbuf + tbytes);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int k = 0; k < cnt; k++) {
+      const int stage = k & 1;
+      if (k + 1 < cnt) {
+        const int i1 = s_list[k + 1];
+        const uint32_t d = sbuf + (uint32_t)(stage ^ 1) * 2u * tbytes;
+        perm_issue<E>(stb, s_in[i1], hdep, ntile, pg.t, d);
+        if (s_in[i1] != s_out[i1]) perm_issue<E>(stb, s_out[i1], hdep, ntile, pg.t, d + tbytes);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 1;" ::: "memory");   // pair k's copies (this thread's)
+      __syncthreads();                                        // ... and every thread's
+      const int i = s_list[k];
+      const uint64_t fa = s_in[i], fb = s_out[i];
+      const bool two = fa != fb;
+      const uint32_t* bufA = buf + (size_t)stage * 2 * ntile * W;
+      const uint32_t* bufB = bufA + ntile * W;
+      // A's amplitudes go to the positions of B (= pi of A's indices), and back
+      for (uint32_t v = threadIdx.x; v < nvec; v += kThreads) {
+        const uint32_t u = v * VA;
+        const uint64_t off = hdep[u >> pg.t] | (u & lowm);
+        vec32 ya, yb;
+#pragma unroll
+        for (int e = 0; e < VA; e++) {
+          const uint32_t sidx = perm_slot<E>(src[u + e], pg.t);
+          if constexpr (W == 4) {
+            const uint4 a = *(const uint4*)(bufA + sidx * 4);
+            ya.w[4 * e] = a.x; ya.w[4 * e + 1] = a.y; ya.w[4 * e + 2] = a.z; ya.w[4 * e + 3] = a.w;
+            if (two) {
+              const uint4 b = *(const uint4*)(bufB + sidx * 4);
+              yb.w[4 * e] = b.x; yb.w[4 * e + 1] = b.y; yb.w[4 * e + 2] = b.z; yb.w[4 * e + 3] = b.w;
+            }
+          } else {
+            const uint2 a = *(const uint2*)(bufA + sidx * 2);
+            ya.w[2 * e] = a.x; ya.w[2 * e + 1] = a.y;
+            if (two) {
+              const uint2 b = *(const uint2*)(bufB + sidx * 2);
+              yb.w[2 * e] = b.x; yb.w[2 * e + 1] = b.y;
+            }
+          }
+        }
+        qc_st32(st + ((fb | off) / VA), ya);
+        if (two) qc_st32(st + ((fa | off) / VA), yb);
+      }
+      __syncthreads();                                        // stage free for pair k + 2
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  }
+}
+
 // ---------------------------------------------------------------- host side
 inline int grid_for(uint64_t work, int threads) {
   const uint64_t want = (work + threads - 1) / threads;
@@ -984,6 +1258,142 @@ int launch_linear_phase(qc_state* s, const qc_op& op) {
   return QC_OK;
 }
 
+
+// Dense 1-qubit gate on the anchor + linear phase run, one sweep (op.pre = 1).
+template <class Ar>
+int launch_dense_linphase(qc_state* s, const qc_op& op) {
+  if constexpr (std::is_same<Ar, ArC128x>::value) {
+    if (s->packed) return launch_dense_linphase<ArC128p>(s, op);
+  }
+  constexpr int V = Ar::V;
+  constexpr int L = V == 4 ? 2 : 1;
+  constexpr int R = kDlR;
+  constexpr int W = L + 2;                   // window bits: in-vector + log2 R
+  static_assert((1 << W) == V * R, "window table size");
+  using Hi = typename HiAr<Ar>::type;
+  if (op.anchor < W) return qc_fail(QC_ERR_ARG, "internal: merged phase sweep on anchor bit %d", op.anchor);
+  DLGeom dg;
+  std::memset(&dg, 0, sizeof(dg));
+  int tpos[1] = {op.anchor};
+  Plan P;
+  if (int rc = build_geom(s, L, tpos, 1, nullptr, nullptr, 0, P)) return rc;
+  if (P.KH != 1 || P.g.ntiles % R) return qc_fail(QC_ERR_ARG, "internal: merged phase sweep geometry");
+  dg.g = P.g;
+  auto tab = std::make_unique<DLTab<Ar>>();
+  std::memset(tab.get(), 0, sizeof(DLTab<Ar>));
+  // window table: theta0 and the linear bits below W
+  for (int x = 0; x < V * R; x++) {
+    double ph = op.theta0;
+    for (int j = 0; j < op.nlin; j++)
+      if (op.lin_pos[j] < W && ((x >> op.lin_pos[j]) & 1)) ph += op.lin_theta[j];
+    tab->w[x] = Ar::make_coef(std::cos(ph), std::sin(ph));
+  }
+  // high tables: the linear bits at W and above, <= 8 per table, ascending
+  int order[QC_MAX_LIN], nh = 0;
+  for (int j = 0; j < op.nlin; j++)
+    if (op.lin_pos[j] >= W) order[nh++] = j;
+  std::sort(order, order + nh, [&](int a, int b) { return op.lin_pos[a] < op.lin_pos[b]; });
+  dg.nhg = (nh + 7) / 8;
+  if (dg.nhg > kDlGroups) return qc_fail(QC_ERR_ARG, "internal: %d linear bits", nh);
+  int ntab = 0;
+  for (int g = 0; g < dg.nhg; g++) {
+    const int b0 = g * 8, nb = std::min(8, nh - b0);
+    dg.hbits[g] = nb;
+    dg.hoff[g] = ntab;
+    bool contig = true;
+    for (int b = 0; b < nb; b++) {
+      dg.hpos[g][b] = op.lin_pos[order[b0 + b]];
+      if (b > 0 && dg.hpos[g][b] != dg.hpos[g][b - 1] + 1) contig = false;
+    }
+    dg.hcontig[g] = contig ? 1 : 0;
+    for (int m = 0; m < (1 << nb); m++) {
+      double ph = 0.0;
+      for (int b = 0; b < nb; b++) if ((m >> b) & 1) ph += op.lin_theta[order[b0 + b]];
+      tab->hi[ntab++] = Hi::make_coef(std::cos(ph), std::sin(ph));
+    }
+  }
+  MatD<Ar, 2> M;
+  for (int i = 0; i < 4; i++) M.m[i] = Ar::make_coef(op.U[2 * i], op.U[2 * i + 1]);
+  const uint64_t nruns = P.g.ntiles / R;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((nruns + kThreads - 1) / kThreads,
+                                                                   (uint64_t)qc_num_sms() * 8));
+  k_dense_linphase<Ar, R><<<grid, kThreads, 0, s->stream>>>((vec32*)s->ptr, dg, M, *tab, ntab);
+  QC_LAUNCHED("k_dense_linphase");
+  return QC_OK;
+}
+
+
+// A run of disjoint SWAPs as one bit-permutation sweep (QC_OP_PERMUTE).
+template <int E>
+int launch_permute(qc_state* s, const qc_op& op) {
+  constexpr int VA = 32 / E;
+  const int n = s->n;
+  int pi[64];
+  for (int b = 0; b < n; b++) pi[b] = b;
+  for (int i = 0; i < op.nperm; i++) {
+    const int a = op.perm_a[i], b = op.perm_b[i];
+    if (a < 0 || b < 0 || a >= n || b >= n || a == b || pi[a] != a || pi[b] != b)
+      return qc_fail(QC_ERR_ARG, "internal: permutation pairs are not disjoint");
+    pi[a] = b;
+    pi[b] = a;
+  }
+  // low bits: segments of 2^5 amplitudes (256 or 512 bytes), at least one vector
+  const int t = std::min(n, kPermT);
+  if ((1 << t) < VA) return qc_fail(QC_ERR_ARG, "internal: state below one vector");
+  uint64_t tmask = (1ull << t) - 1ull;
+  for (int b = 0; b < t; b++) tmask |= 1ull << pi[b];
+  PermGeom pg;
+  std::memset(&pg, 0, sizeof(pg));
+  pg.t = t;
+  for (int b = t; b < n; b++)
+    if ((tmask >> b) & 1) pg.hpos[pg.h++] = b;
+  for (int b = 0; b < n; b++)
+    if ((tmask >> b) & 1) pg.ins[pg.nins++] = b;
+  // outside bits (compressed order) and the pairs among them
+  int cidx[64], nO = 0;
+  for (int b = 0; b < n; b++) cidx[b] = ((tmask >> b) & 1) ? -1 : nO++;
+  for (int b = 0; b < n; b++)
+    if (cidx[b] >= 0 && pi[b] > b) { pg.pa[pg.npairs] = cidx[b]; pg.pb[pg.npairs] = cidx[pi[b]]; pg.npairs++; }
+  pg.ntiles = 1ull << nO;
+  const uint32_t ntile = 1u << (t + pg.h);
+  if (ntile > (uint32_t)kPermMaxTile) return qc_fail(QC_ERR_ARG, "internal: permutation tile of %u", ntile);
+  // src[u]: local index of the source of output local index u; local index =
+  // (high tile bits, in hpos order) << t | low bits
+  auto local_to_bits = [&](uint32_t u) {
+    uint64_t y = u & ((1u << t) - 1u);
+    for (int i = 0; i < pg.h; i++) y |= (uint64_t)((u >> (t + i)) & 1u) << pg.hpos[i];
+    return y;
+  };
+  auto bits_to_local = [&](uint64_t y) {
+    uint32_t u = (uint32_t)(y & ((1ull << t) - 1ull));
+    for (int i = 0; i < pg.h; i++) u |= (uint32_t)((y >> pg.hpos[i]) & 1ull) << (t + i);
+    return u;
+  };
+  auto tab = std::make_unique<PermTab>();
+  for (uint32_t u = 0; u < ntile; u++) {
+    const uint64_t y = local_to_bits(u);
+    uint64_t x = 0;                            // pi(y) on the tile bits (pi is its own inverse)
+    for (int b = 0; b < n; b++)
+      if ((tmask >> b) & 1) x |= ((y >> b) & 1ull) << pi[b];
+    tab->src[u] = (uint16_t)bits_to_local(x);
+  }
+  const size_t smem = 4 * (size_t)ntile * E + (size_t)ntile * 2 + 8 + ((size_t)8 << pg.h) +
+                      kPermBatch * (8 + 8 + 4) + 4;
+  static bool attr[2][64] = {};
+  const int dev = s->device;
+  if (dev >= 0 && dev < 64 && !attr[E == 16][dev]) {
+    QC_CUDA(cudaFuncSetAttribute(k_permute<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(4 * (size_t)kPermMaxTile * E + kPermMaxTile * 2 + 8 + (8 << kPermT) +
+                                       kPermBatch * 20 + 4)));
+    attr[E == 16][dev] = true;
+  }
+  const uint64_t nbatches = (pg.ntiles + kPermBatch - 1) / kPermBatch;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(nbatches, (uint64_t)qc_num_sms() * 4));
+  k_permute<E><<<grid, kThreads, smem, s->stream>>>((vec32*)s->ptr, pg, *tab);
+  QC_LAUNCHED("k_permute");
+  return QC_OK;
+}
+
 // Reorder a 2-qubit matrix so that its first target has the higher bit position.
 void order_two_qubit(qc_op& op) {
   if (op.k != 2 || op.tpos[0] > op.tpos[1]) return;
@@ -1059,6 +1469,15 @@ int qc_tc_timeouts(int* count) {
 }
 
 int qc_launch_op(qc_state* s, const qc_op& op) {
+  if (op.kind == QC_OP_PERMUTE) {
+    if (s->dtype == QC_C64) return launch_permute<8>(s, op);
+    return launch_permute<16>(s, op);
+  }
+  if (op.kind == QC_OP_LINEAR_PHASE && op.pre) {
+    if (s->dtype == QC_C64) return launch_dense_linphase<ArC64>(s, op);
+    if (s->arith == QC_ARITH_NATIVE) return launch_dense_linphase<ArC128>(s, op);
+    return launch_dense_linphase<ArC128x>(s, op);
+  }
   if (op.kind == QC_OP_LINEAR_PHASE) {
     if (s->n < 3) return qc_fail(QC_ERR_ARG, "internal: linear phase op on n < 3");
     if (s->dtype == QC_C64) return launch_linear_phase<ArC64>(s, op);

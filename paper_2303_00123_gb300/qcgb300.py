@@ -340,7 +340,9 @@ def expect_passes(n: int, dtype: int, hamiltonian) -> int:
 def fuse_plan(n: int, gates, fuse_k: int):
     """Host-only launch plan: a list with one entry per launch, either a
     matrix block (qubits, controls, cstates, U) or a linear phase run
-    ("phase", anchor, [(qubit, theta), ...], theta0)."""
+    ("phase", anchor, [(qubit, theta), ...], theta0, pre), where pre is None or
+    a 2x2 matrix applied to the anchor first, in the same sweep, or a run of
+    SWAPs on disjoint pairs applied as one bit permutation ("swap", [(a, b), ...])."""
     arr, keep = gate_records(gates)
     nb = ctypes.c_int(0)
     cap = max(1, len(gates))
@@ -348,8 +350,15 @@ def fuse_plan(n: int, gates, fuse_k: int):
     _check(lib.qc_fuse_plan(n, arr, len(gates), int(fuse_k), blocks, cap, ctypes.byref(nb)))
     out = []
     for b in blocks[:nb.value]:
+        if b.kind == 2:
+            out.append(("swap", [(b.lin_qubits[2 * j], b.lin_qubits[2 * j + 1]) for j in range(b.nlin // 2)]))
+            continue
         if b.kind == 1:
-            out.append(("phase", b.anchor, [(b.lin_qubits[j], b.lin_theta[j]) for j in range(b.nlin)], b.theta0))
+            pre = None
+            if b.k == 1:      # 2x2 matrix on the anchor, applied before the phase
+                pre = np.array([complex(b.U[2 * i], b.U[2 * i + 1]) for i in range(4)]).reshape(2, 2)
+            out.append(("phase", b.anchor, [(b.lin_qubits[j], b.lin_theta[j]) for j in range(b.nlin)], b.theta0,
+                        pre))
             continue
         d = 1 << b.k
         U = np.array(b.U[:2 * d * d], dtype=np.float64).view(np.complex128).reshape(d, d)

@@ -76,7 +76,7 @@ def test_fusion_plan_reproduces_the_circuit(q, fuse_k):
     plan = q.fuse_plan(n, gates, fuse_k)
     if fuse_k >= 2:
         assert len(plan) < (0.6 if fuse_k == 2 else 0.35) * len(gates)
-        assert max(len(b[0]) + len(b[1]) for b in plan if b[0] != "phase") <= max(fuse_k, 3)
+        assert max(len(b[0]) + len(b[1]) for b in plan if b[0] not in ("phase", "swap")) <= max(fuse_k, 3)
     else:
         assert len(plan) == len(gates)
     phi = C.random_state(n, 13)
@@ -88,10 +88,18 @@ def test_fusion_plan_reproduces_the_circuit(q, fuse_k):
 
 def apply_plan(O, psi, n, plan):
     """Apply a fusion plan with the oracle; a linear phase run is applied as
-    the phase gates it stands for (P(theta) on the anchor, controlled)."""
+    the gates it stands for: its 2x2 matrix on the anchor, if any, then P(theta)
+    on the anchor, controlled."""
+    swap = np.eye(4)[[0, 2, 1, 3]]
     for entry in plan:
+        if entry[0] == "swap":
+            for a, b in entry[1]:
+                O.apply_matrix(psi, n, swap, (a, b))
+            continue
         if entry[0] == "phase":
-            _, anchor, lin, theta0 = entry
+            _, anchor, lin, theta0, pre = entry
+            if pre is not None:
+                O.apply_matrix(psi, n, pre, (anchor,))
             P = lambda t: np.diag([1, np.exp(1j * t)])
             if theta0 != 0:
                 O.apply_matrix(psi, n, P(theta0), (anchor,))
@@ -153,3 +161,36 @@ def test_expect_pass_counts(q):
     assert q.expect_passes(30, q.C128, []) == 0
     with pytest.raises(q.QCError):
         q.expect_passes(30, q.C128, [(1.0, [("X", 30)])])
+
+
+def test_qft_plan_merges_hadamards_and_swaps(q):
+    """QFT (Fig. 1) at n=30 with fusion: each stage's H joins its phase run
+    (anchors up to qubit n-5), the last stages fuse into a 2-qubit block, and
+    the 15 final SWAPs become one bit permutation."""
+    from paper_2303_00123_gb300 import circuits as C
+    n = 30
+    plan = q.fuse_plan(n, C.qft(n), 2)
+    runs = [e for e in plan if e[0] == "phase"]
+    swaps = [e for e in plan if e[0] == "swap"]
+    assert len(swaps) == 1 and sorted(swaps[0][1]) == [(i, n - 1 - i) for i in range(n // 2)]
+    assert sum(e[4] is not None for e in runs) == n - 4
+    assert all(e[4] is None for e in runs if e[1] > n - 5)
+    assert len(plan) == 1 + len(runs) + 2 + 1      # runs, H(26), H(27), block(28, 29), permutation
+
+
+def test_swap_runs_need_disjoint_pairs(q):
+    """Only SWAPs on disjoint pairs merge; a qubit seen twice starts a new run,
+    and a single SWAP stays a matrix block."""
+    from oracle import oracle as O
+    from paper_2303_00123_gb300 import circuits as C
+    n = 8
+    gates = [C.Gate("SWAP", (0, 5)), C.Gate("SWAP", (1, 7)), C.Gate("SWAP", (5, 2)), C.Gate("SWAP", (3, 4)),
+             C.Gate("H", (0,)), C.Gate("SWAP", (6, 1))]
+    plan = q.fuse_plan(n, gates, 2)
+    kinds = [e[0] if isinstance(e[0], str) else "matrix" for e in plan]
+    assert kinds == ["swap", "swap", "matrix", "matrix"]
+    assert plan[0][1] == [(0, 5), (1, 7)] and plan[1][1] == [(5, 2), (3, 4)]
+    phi = C.random_state(n, 5)
+    psi = phi.copy()
+    apply_plan(O, psi, n, plan)
+    np.testing.assert_allclose(psi, O.run_circuit(n, gates, phi), atol=1e-12)
