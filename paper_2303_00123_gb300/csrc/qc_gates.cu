@@ -661,7 +661,8 @@ struct DLTab {
 template <class Ar, int R>
 __global__ void __launch_bounds__(kThreads, 2)
 k_dense_linphase(vec32* __restrict__ st, const __grid_constant__ DLGeom dg, const __grid_constant__ MatD<Ar, 2> M,
-                 const __grid_constant__ DLTab<Ar> tab, int nhi) {
+                 const __grid_constant__ MatD<typename HiAr<Ar>::type, 2> Mh, const __grid_constant__ DLTab<Ar> tab,
+                 int nhi) {
   constexpr int V = Ar::V;
   constexpr int L = V == 4 ? 2 : 1;
   using Hi = typename HiAr<Ar>::type;
@@ -692,15 +693,17 @@ k_dense_linphase(vec32* __restrict__ st, const __grid_constant__ DLGeom dg, cons
       }
       h = Hi::template dot<1>(&Th[dg.hoff[gi] + m], &h);
     }
-    const typename Ar::coef_t hc = PhaseCoef<Ar>::of(h);
+    // U's second row times that factor: the anchor-1 output in one dot
+    typename Ar::coef_t row1[2];
+#pragma unroll
+    for (int c = 0; c < 2; c++) row1[c] = PhaseCoef<Ar>::of(Hi::template dot<1>(&Mh.m[2 + c], &h));
 #pragma unroll
     for (int k = 0; k < R; k++) {
 #pragma unroll
       for (int e = 0; e < V; e++) {
         val_t in[2] = {Ar::load(r0[k], e), Ar::load(r1[k], e)};
         const val_t o0 = Ar::template dot<2>(&M.m[0], in);
-        val_t o1 = Ar::template dot<2>(&M.m[2], in);
-        o1 = Ar::template dot<1>(&hc, &o1);
+        val_t o1 = Ar::template dot<2>(row1, in);
         o1 = Ar::template dot<1>(&Tw[k * V + e], &o1);
         Ar::store(r0[k], e, o0);
         Ar::store(r1[k], e, o1);
@@ -1313,11 +1316,15 @@ int launch_dense_linphase(qc_state* s, const qc_op& op) {
     }
   }
   MatD<Ar, 2> M;
-  for (int i = 0; i < 4; i++) M.m[i] = Ar::make_coef(op.U[2 * i], op.U[2 * i + 1]);
+  MatD<Hi, 2> Mh;
+  for (int i = 0; i < 4; i++) {
+    M.m[i] = Ar::make_coef(op.U[2 * i], op.U[2 * i + 1]);
+    Mh.m[i] = Hi::make_coef(op.U[2 * i], op.U[2 * i + 1]);
+  }
   const uint64_t nruns = P.g.ntiles / R;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((nruns + kThreads - 1) / kThreads,
                                                                    (uint64_t)qc_num_sms() * 8));
-  k_dense_linphase<Ar, R><<<grid, kThreads, 0, s->stream>>>((vec32*)s->ptr, dg, M, *tab, ntab);
+  k_dense_linphase<Ar, R><<<grid, kThreads, 0, s->stream>>>((vec32*)s->ptr, dg, M, Mh, *tab, ntab);
   QC_LAUNCHED("k_dense_linphase");
   return QC_OK;
 }
