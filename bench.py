@@ -272,7 +272,7 @@ def run_gpu(args):
         "value": round(value, 3), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed / args.steps * 1e3, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128-" + args.arith, "data": "synthetic",
-        "config": {"workload": "configs[1]: n=30 complex128 QFT (seeded basis state) + brickwork depth 40 (Haar U(2) "
+        "config": {"workload": "n=30 complex128 QFT (seeded basis state) + brickwork depth 40 (Haar U(2) "
                                "layers + CNOT pairs), gate by gate", "n": n, "gates_per_step": gates_per_step,
                    "fuse_k": args.fuse, "arith": args.arith, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (17.2 GB state vs 129 MB)"},
@@ -577,8 +577,29 @@ def extra_measurements(q, st, stream, brick, x):
     qft_run(2)
     q0 = _event_ms(stream, lambda: qft_run(0))
     q2 = _event_ms(stream, lambda: qft_run(2))
-    fused["qft_c128_k2_phase_runs"] = {"ms": round(q2, 1), "unfused_ms": round(q0, 1), "speedup": round(q0 / q2, 2),
-                                       "launches": len(q.fuse_plan(N_QUBITS, qft, 2))}
+    fused["qft_c128_k2"] = {"ms": round(q2, 1), "unfused_ms": round(q0, 1), "speedup": round(q0 / q2, 2),
+                            "launches": len(q.fuse_plan(N_QUBITS, qft, 2))}
+    # expectation of the TFIM chain on the same 30-qubit state: tiled passes vs
+    # one sweep per distinct flip mask
+    Ht = C.tfim(N_QUBITS, 1.0)
+    st.expect(Ht)
+    te0 = time.perf_counter()
+    for _ in range(3):
+        e_tile = st.expect(Ht)
+    te_tile = (time.perf_counter() - te0) / 3 * 1e3
+    st.expect_noalloc(Ht)
+    te0 = time.perf_counter()
+    for _ in range(2):
+        e_sweep = st.expect_noalloc(Ht)
+    te_sweep = (time.perf_counter() - te0) / 2 * 1e3
+    passes = q.expect_passes(N_QUBITS, q.C128, Ht)
+    peak, _ = measured_peaks()
+    gb = passes * (1 << N_QUBITS) * 16 / 1e9
+    out["expect"] = {"workload": "TFIM chain (29 ZZ + 30 X terms), n=30 complex128", "passes": passes,
+                     "ms": round(te_tile, 2), "GBps": round(gb / te_tile * 1e3, 1),
+                     "frac_of_measured_hbm": round(gb / te_tile * 1e3 / peak, 4),
+                     "per_flip_mask_sweeps_ms": round(te_sweep, 1), "speedup": round(te_sweep / te_tile, 2),
+                     "abs_diff": abs(e_tile - e_sweep)}
     t64 = torch.empty(1 << N_QUBITS, dtype=torch.complex64, device="cuda")
     s64 = q.State.from_tensor(t64)
     s64.set_stream(stream)
@@ -590,7 +611,8 @@ def extra_measurements(q, st, stream, brick, x):
     s64.free()
     del t64
     torch.cuda.empty_cache()
-    out["fused"] = {"workload": "n=30: brickwork depth 40 (greedy k-qubit blocks); QFT (linear phase runs)", **fused}
+    out["fused"] = {"workload": "n=30: brickwork depth 40 (greedy k-qubit blocks); QFT (each H merged with its "
+                                "phase run, final SWAPs as one bit permutation)", **fused}
     # batched: 1024 circuits, one persistent launch vs one launch per gate
     specs = C.batch_specs(1024, seed=4)
     circs = [C.random_mix(n, d, seed=sd) for n, d, sd in specs]
@@ -673,7 +695,7 @@ def run_reference(args):
         "value": round(value, 4), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "configs[1] sample, FP64 CPU oracle", "n": N_QUBITS},
+        "config": {"workload": "n=30 complex128 QFT + brickwork sample, FP64 CPU oracle", "n": N_QUBITS},
         "cpu_baseline": cpu, "e2e": {"value": round(value, 4), "unit": "gates/s", "h2d_bytes_per_step": 0,
                                      "d2h_bytes_per_step": 0}}))
 
