@@ -419,7 +419,8 @@ def run_fused_case(args):
     stream = torch.cuda.Stream()
     st.set_stream(stream)
     res = {}
-    for k in (0, 2, 3, 4, 5):
+    ks = (args.fuse,) if args.fuse else (0, 2, 3, 4, 5)   # --fuse K: that width only
+    for k in ks:
         for _ in range(args.warmup):
             st.set_basis(0)
             st.apply_circuit(gates, fuse_k=k)
@@ -444,7 +445,7 @@ def run_fused_case(args):
         ne = args.n_err
         g2 = C.qft(ne) if args.circuit == "qft" else C.brickwork(ne, BRICK_DEPTH, seed=SEED_BRICK)
         ref = O.run_circuit(ne, g2)
-        for k in (0, 2, 3, 4, 5):
+        for k in ks:
             s2 = q.State(ne, dt)
             s2.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
             s2.set_fused_tc(not args.no_tc)
@@ -457,7 +458,8 @@ def run_fused_case(args):
                       "gates": len(gates),
                       "tensor_cores": (not args.no_tc) and args.dtype == "c64",
                       "by_fuse_k": res, "n_err": args.n_err, "error_vs_oracle": err,
-                      "speedup_best_vs_unfused": round(res["0"]["ms"] / min(v["ms"] for v in res.values()), 2)}))
+                      "speedup_best_vs_unfused": (round(res["0"]["ms"] / min(v["ms"] for v in res.values()), 2)
+                                                  if "0" in res else None)}))
 
 
 def run_expect_case(args):
