@@ -38,6 +38,8 @@ N_QUBITS = 30
 BRICK_DEPTH = 40
 SEED_BASIS = 1000
 SEED_BRICK = 1001
+TFXY_STEPS = 10          # TFXY Trotter circuit: 10 steps = 1760 gates at n=30
+SEED_TFXY = 1003
 HBM_FALLBACK = 6800.0
 
 
@@ -401,6 +403,15 @@ def run_batch_case(args):
                       "speedup": round(base_tot / tot, 2), "autotune_s": round(tune_s, 2)}))
 
 
+def circuit_for(name, n):
+    """Benchmark circuit families: QFT, brickwork depth 40, TFXY Trotter (10 steps)."""
+    if name == "qft":
+        return C.qft(n)
+    if name == "tfxy":
+        return C.tfxy_trotter(n, TFXY_STEPS, seed=SEED_TFXY)
+    return C.brickwork(n, BRICK_DEPTH, seed=SEED_BRICK)
+
+
 def run_fused_case(args):
     """Brickwork depth 40 at n qubits with greedy fusion k = 0 (gate by gate),
     2, 3, 4, 5: time, launches, gates/s, and effective HBM GB/s (sum of the
@@ -411,7 +422,7 @@ def run_fused_case(args):
     n = args.n
     dt = q.C64 if args.dtype == "c64" else q.C128
     elem = 8 if dt == q.C64 else 16
-    gates = C.qft(n) if args.circuit == "qft" else C.brickwork(n, BRICK_DEPTH, seed=SEED_BRICK)
+    gates = circuit_for(args.circuit, n)
     t = torch.empty(1 << n, dtype=torch.complex64 if dt == q.C64 else torch.complex128, device="cuda")
     st = q.State.from_tensor(t)
     st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
@@ -443,7 +454,7 @@ def run_fused_case(args):
     if args.n_err > 0:
         from oracle import oracle as O
         ne = args.n_err
-        g2 = C.qft(ne) if args.circuit == "qft" else C.brickwork(ne, BRICK_DEPTH, seed=SEED_BRICK)
+        g2 = circuit_for(args.circuit, ne)
         ref = O.run_circuit(ne, g2)
         for k in ks:
             s2 = q.State(ne, dt)
@@ -610,11 +621,26 @@ def extra_measurements(q, st, stream, brick, x):
     u5 = _event_ms(stream, lambda: brick_run(s64, 5))
     fused["c64_k5_tensor_cores"] = {"ms": round(u5, 1), "unfused_ms": round(u0, 1), "speedup": round(u0 / u5, 2),
                                     "launches": len(q.fuse_plan(N_QUBITS, brick, 5))}
+    # TFXY Trotter circuit (Sec. 4, 10 steps): complex128 k=2, complex64 k=5 on the tensor cores
+    tfxy = C.tfxy_trotter(N_QUBITS, TFXY_STEPS, seed=SEED_TFXY)
+    def tfxy_run(state, k):
+        state.set_basis(0)
+        state.apply_circuit(tfxy, fuse_k=k)
+    tfxy_run(s64, 5)
+    v0 = _event_ms(stream, lambda: tfxy_run(s64, 0))
+    v5 = _event_ms(stream, lambda: tfxy_run(s64, 5))
+    fused["tfxy_c64_k5_tensor_cores"] = {"ms": round(v5, 1), "unfused_ms": round(v0, 1), "speedup": round(v0 / v5, 2),
+                                         "launches": len(q.fuse_plan(N_QUBITS, tfxy, 5))}
     s64.free()
     del t64
     torch.cuda.empty_cache()
+    tfxy_run(st, 2)
+    w0 = _event_ms(stream, lambda: tfxy_run(st, 0))
+    w2 = _event_ms(stream, lambda: tfxy_run(st, 2))
+    fused["tfxy_c128_k2"] = {"ms": round(w2, 1), "unfused_ms": round(w0, 1), "speedup": round(w0 / w2, 2),
+                             "launches": len(q.fuse_plan(N_QUBITS, tfxy, 2))}
     out["fused"] = {"workload": "n=30: brickwork depth 40 (greedy k-qubit blocks); QFT (each H merged with its "
-                                "phase run, final SWAPs as one bit permutation)", **fused}
+                                "phase run, final SWAPs as one bit permutation); TFXY Trotter, 10 steps", **fused}
     # batched: 1024 circuits, one persistent launch vs one launch per gate
     specs = C.batch_specs(1024, seed=4)
     circs = [C.random_mix(n, d, seed=sd) for n, d, sd in specs]
@@ -719,7 +745,7 @@ def main():
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--n-err", dest="n_err", type=int, default=0)
-    ap.add_argument("--circuit", default="brickwork", choices=["brickwork", "qft"])
+    ap.add_argument("--circuit", default="brickwork", choices=["brickwork", "qft", "tfxy"])
     ap.add_argument("--no-tc", dest="no_tc", action="store_true", help="complex64 blocks on CUDA cores")
     ap.add_argument("--no-packed", dest="no_packed", action="store_true", help="scalar FP32 float-float")
     args = ap.parse_args()

@@ -73,6 +73,29 @@ def brickwork(n: int, depth: int, seed: int) -> list:
     return gates
 
 
+def tfxy_trotter(n: int, steps: int, seed: int) -> list:
+    """Trotter time evolution of a nearest-neighbour TFXY chain, the second
+    benchmark circuit of Sec. 4 (its figure shows two steps on four qubits).
+    One step: RZ on every qubit; on each even pair (i, i+1), i even: CNOT(i ->
+    i+1), RX on i and RZ on i+1, CNOT(i -> i+1); RZ on every qubit; the same
+    block on each odd pair.  Each block equals exp(-i a/2 X_i X_{i+1})
+    exp(-i b/2 Z_i Z_{i+1}) for its RX angle a and RZ angle b.  The paper
+    prints no angles: every angle is drawn uniformly from (-pi, pi), seeded."""
+    rng = np.random.default_rng(seed)
+    ang = lambda: float(rng.uniform(-math.pi, math.pi))
+    gates = []
+    for _ in range(steps):
+        for start in (0, 1):
+            for q in range(n):
+                gates.append(Gate("RZ", (q,), theta=ang()))
+            for i in range(start, n - 1, 2):
+                gates.append(Gate("X", (i + 1,), controls=(i,), cstates=(1,)))
+                gates.append(Gate("RX", (i,), theta=ang()))
+                gates.append(Gate("RZ", (i + 1,), theta=ang()))
+                gates.append(Gate("X", (i + 1,), controls=(i,), cstates=(1,)))
+    return gates
+
+
 def random_mix(n: int, ngates: int, seed: int) -> list:
     """Seeded gate mix: 60% Haar U(2) on a uniform target; 20% singly
     controlled gates (half CNOT, half controlled Haar U(2), control state 0/1

@@ -538,3 +538,41 @@ def test_fused_qft_with_linear_phase_runs(q, mode):
     gates += [Gate("P", (int(t),), controls=(8,), theta=float(rng.uniform(-3, 3))) for t in (0, 10, 3, 2)]
     phi = C.random_state(n, 5)
     assert maxerr(gpu_run(q, n, gates, mode, psi0=phi, fuse_k=3), O.run_circuit(n, gates, phi)) <= TOL[mode]
+
+
+# ------------------------------------------------------------------ TFXY Trotter circuit
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("fuse_k", [0, 2, 3, 5])
+def test_tfxy_trotter_n13(q, mode, fuse_k):
+    """The Hamiltonian-simulation circuit of Sec. 4 (3 Trotter steps, seeded
+    angles) on a random 13-qubit state, gate by gate and fused (complex64
+    blocks of k >= 3 on the tensor cores), against the oracle."""
+    n = 13
+    gates = C.tfxy_trotter(n, 3, seed=5)
+    phi = C.random_state(n, 6)
+    assert maxerr(gpu_run(q, n, gates, mode, psi0=phi, fuse_k=fuse_k), O.run_circuit(n, gates, phi)) <= TOL[mode]
+
+
+@pytest.mark.parametrize("dtype,fuse_k", [("c128", 2), ("c64", 5)])
+def test_tfxy_n28_then_inverse_returns_basis_state(q, dtype, fuse_k):
+    """n=28: two fused Trotter steps then their inverse map |x> back to |x>
+    (a property valid at any size); sampled amplitudes."""
+    import torch
+    from tests.test_oracle_pins import _inverse
+    n = 28
+    rng = np.random.default_rng(2801)
+    x = int(rng.integers(0, 1 << n))
+    gates = C.tfxy_trotter(n, 2, seed=9)
+    t = torch.zeros(1 << n, dtype=torch.complex128 if dtype == "c128" else torch.complex64, device="cuda")
+    st = q.State.from_tensor(t)
+    st.set_basis(x)
+    st.apply_circuit(gates, fuse_k=fuse_k)
+    assert abs(_sample(t, [x])[0]) < 0.9          # the state moved
+    st.apply_circuit(_inverse(gates), fuse_k=fuse_k)
+    ys = np.concatenate([[x], rng.integers(0, 1 << n, size=4095)])
+    got = _sample(t, ys)
+    ref = (ys == x).astype(np.complex128)
+    assert maxerr(got, ref) <= (1e-12 if dtype == "c128" else 2e-5)
+    st.free()
+    del t
+    torch.cuda.empty_cache()

@@ -327,3 +327,43 @@ def test_generators_follow_their_recipes():
     assert 0.5 < kinds.count("U") / 300 < 0.7 and 0.1 < kinds.count("C") / 300 < 0.3
     h = C.hea(4, 3, C.hea_thetas(4, 3, seed=2))
     assert len(O.parametric_indices(h)) == 2 * 4 * 3
+
+
+def test_tfxy_block_is_a_product_of_two_qubit_exponentials():
+    """Each block of the TFXY Trotter circuit (Sec. 4 figure): CNOT(i -> j),
+    RX(a) on i, RZ(b) on j, CNOT(i -> j) equals exp(-i a/2 X_i X_j)
+    exp(-i b/2 Z_i Z_j) -- conjugation by the CNOT maps X_i to X_i X_j and Z_j
+    to Z_i Z_j.  Checked against matrix exponentials (scipy) on a 4-qubit
+    state for an adjacent and a distant pair."""
+    from scipy.linalg import expm
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    Z = np.diag([1.0, -1.0]).astype(complex)
+    n = 4
+    rng = np.random.default_rng(31)
+    for i, j in ((1, 2), (3, 0)):
+        a, b = rng.uniform(-math.pi, math.pi, size=2)
+        block = [Gate("X", (j,), controls=(i,), cstates=(1,)), Gate("RX", (i,), theta=a),
+                 Gate("RZ", (j,), theta=b), Gate("X", (j,), controls=(i,), cstates=(1,))]
+
+        def two(A, B):          # A on qubit i, B on qubit j, identity elsewhere (qubit 0 = MSB)
+            ops = [np.eye(2, dtype=complex)] * n
+            ops[i], ops[j] = A, B
+            m = ops[0]
+            for o in ops[1:]:
+                m = np.kron(m, o)
+            return m
+        U = expm(-0.5j * a * two(X, X)) @ expm(-0.5j * b * two(Z, Z))
+        phi = C.random_state(n, 40 + i)
+        np.testing.assert_allclose(O.run_circuit(n, block, phi), U @ phi, atol=1e-13)
+
+
+def test_tfxy_layout_follows_the_figure():
+    """Two Trotter steps on four qubits: RZ layer, blocks on pairs (0,1) and
+    (2,3), RZ layer, block on (1,2) -- twice; 40 gates."""
+    g = C.tfxy_trotter(4, 2, seed=0)
+    assert len(g) == 40
+    sig = [(x.name, x.qubits, tuple(x.controls)) for x in g[:20]]
+    rz = lambda qs: [("RZ", (q,), ()) for q in qs]
+    blk = lambda i, j: [("X", (j,), (i,)), ("RX", (i,), ()), ("RZ", (j,), ()), ("X", (j,), (i,))]
+    assert sig == rz(range(4)) + blk(0, 1) + blk(2, 3) + rz(range(4)) + blk(1, 2)
+    assert [(x.name, x.qubits, tuple(x.controls)) for x in g[20:]] == sig
