@@ -26,6 +26,8 @@
 #include <cstring>
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 #include "qc_common.cuh"
 
 namespace {
@@ -528,6 +530,280 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
         for (int j = 0; j < NC; j++)
           st[curbase + moff[c + j]] = make_float2(__uint_as_float(re0[j]) + __uint_as_float(re1[j]),
                                                   __uint_as_float(im0[j]) + __uint_as_float(im1[j]));
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL) : "memory");
+}
+
+// ---------------------------------------------------------------- fused tiles, tensor cores, complex128
+// complex128 dense k-qubit block (k = 3..5) on the tensor cores, with exact
+// integer slices (the error-free splitting idea of Ozaki et al.): the same
+// GEMM as k_fused_tc (128 groups x 2D reals times R^T), but every operand
+// entry is written as six balanced base-2^9 digits, |digit| <= 256, which
+// fp16 holds exactly:
+//   x = 2^E_g * sum_s a_s 2^(-9 s)   (E_g from the largest entry of group g),
+//   r = 2^-8  * sum_t b_t 2^(-9 t)   (|r| <= 1 for a unitary),
+// and the products of digit matrices are summed by level d = s + t (d <= 5,
+// 21 products) into six FP32 accumulators in tensor memory.  A digit product
+// is at most 2^16 and K <= 64, so levels 0..3 (at most 4 products each, sums
+// below 2^24) are exact integer sums; levels 4 and 5 may round, 2^-60 below
+// the group's scale.  The epilogue recombines sum_d 2^(-9 d) D_d in
+// float-float (powers of two are exact), converts to double and applies
+// 2^(E_g - 8) to the exponent field.  Error: about 2^-47 of the group's
+// largest entry (the float-float split of the input), like the complex128
+// CUDA-core arithmetic.  Entries below 2^-119 of a group are flushed to zero.
+template <int K>
+struct MatC128 { double2 u[(1 << K) * (1 << K)]; };
+
+constexpr int kTcDig = 6;                         // digits per operand entry
+constexpr int kTcLev = 6;                         // accumulator levels d = s + t <= 5
+
+__device__ __forceinline__ float tc_rnd(float x) {  // nearest integer of |x| < 2^22
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+
+// Digits of (h + l) * scale, h + l a float-float value, |h * scale| <= 256:
+// each step removes the nearest integer and scales the remainder by 2^9.  The
+// lo word joins when the hi word's bits are used up; it is added to the
+// remainder only where the sum is exact, and only steers the digit choice
+// before that, so every digit stays within [-256, 256].
+__device__ __forceinline__ void tc_digits(float h, float l, float scale, float* d) {
+  const float hs = __fmul_rn(h, scale);
+  float ls = __fmul_rn(l, scale);
+  d[0] = tc_rnd(hs);
+  float r = __fmul_rn(__fsub_rn(hs, d[0]), 512.f);      // exact
+  ls = __fmul_rn(ls, 512.f);
+  d[1] = tc_rnd(__fadd_rn(r, ls));
+  float rh = __fmul_rn(__fsub_rn(r, d[1]), 512.f);      // exact: a multiple of 4
+  ls = __fmul_rn(ls, 512.f);
+  d[2] = tc_rnd(__fadd_rn(rh, ls));
+  r = __fadd_rn(__fsub_rn(rh, d[2]), ls);               // small integer + ls: exact
+#pragma unroll
+  for (int i = 3; i < kTcDig; i++) {
+    r = __fmul_rn(r, 512.f);
+    d[i] = tc_rnd(r);
+    r = __fsub_rn(r, d[i]);
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {   // lo -> low half
+  uint32_t v;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(v) : "f"(hi), "f"(lo));
+  return v;
+}
+
+// byte offset of element (row, col) in a K-major no-swizzle fp16 operand with KR columns
+__device__ __forceinline__ uint32_t kmaj16_off(int row, int col, int KR) {
+  return (row >> 3) * (KR >> 3) * 128 + (col >> 3) * 128 + (row & 7) * 16 + (col & 7) * 2;
+}
+
+// sum_d 2^(-9 d) D_d in float-float (Horner from the smallest level), as a double
+__device__ __forceinline__ double tc_combine(const float* D) {
+  float ah = D[kTcLev - 1], al = 0.f;
+#pragma unroll
+  for (int d = kTcLev - 2; d >= 0; d--) {
+    ah = __fmul_rn(ah, 1.f / 512.f);
+    al = __fmul_rn(al, 1.f / 512.f);
+    const float s = __fadd_rn(D[d], ah);
+    const float z = __fsub_rn(s, D[d]);
+    const float e = __fadd_rn(__fsub_rn(D[d], __fsub_rn(s, z)), __fsub_rn(ah, z));
+    ah = s;
+    al = __fadd_rn(al, e);
+  }
+  return ArC128x::f2d(ah) + ArC128x::f2d(al);
+}
+
+// x * 2^e for a double x that stays normal (exponent field arithmetic); 0 stays 0
+__device__ __forceinline__ double tc_scale(double x, int e) {
+  if (x == 0.0) return 0.0;
+  return __hiloint2double(__double2hiint(x) + e * (1 << 20), __double2loint(x));
+}
+
+// Threads per CTA: two per accumulator row (four per row, for twice the
+// warps, measured slower; so did rolling the phases' outer loops).
+template <int K> struct Tc128Cfg {
+  static constexpr int TPR = 2;                   // threads per row (group)
+  static constexpr int NT = 128 * TPR;
+};
+
+template <int K>
+__global__ void __launch_bounds__(Tc128Cfg<K>::NT, 1)
+k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC128<K> U) {
+  constexpr int D = 1 << K;
+  constexpr int TPR = Tc128Cfg<K>::TPR, NT = Tc128Cfg<K>::NT;
+  constexpr int H = D / TPR;                      // members per thread
+  constexpr int KR = 2 * D;                       // GEMM N = K
+  constexpr uint32_t NCOL = kTcLev * KR <= 128 ? 128 : (kTcLev * KR <= 256 ? 256 : 512);
+  constexpr uint32_t SBO = (KR / 8) * 128;
+  constexpr uint32_t ASZ = 128 * KR * 2, BSZ = KR * KR * 2;   // bytes per digit slice
+  static_assert(H % 4 == 0, "four columns per store at least");
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* sA = smem_tc;                    // [digit][128 x KR] fp16
+  unsigned char* sB = sA + kTcDig * ASZ;          // [digit][KR x KR] fp16, row n = output n
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ uint64_t s_moff[D];
+  __shared__ int s_emax[TPR][128];
+  const int t = threadIdx.x;
+  const int w = t >> 5;
+  const int row = t & 127;
+  const int part_of = t >> 7;                     // which slice of the row's members
+  const int m0 = part_of * H;
+  const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
+  // B digits: B[n][k] = R[n][k] * 2^8, R = [[Ur, -Ui], [Ui, Ur]]
+  for (int i = t; i < KR * KR; i += NT) {
+    const int n = i / KR, k = i % KR;
+    const double2 u = U.u[(n % D) * D + (k % D)];
+    const double v = n < D ? (k < D ? u.x : -u.y) : (k < D ? u.y : u.x);
+    const ArC128x::ff f = ArC128x::split((uint32_t)__double2loint(v), (uint32_t)__double2hiint(v));
+    float dg[kTcDig];
+    tc_digits(f.h, f.l, 256.f, dg);
+#pragma unroll
+    for (int s = 0; s < kTcDig; s++)
+      *reinterpret_cast<__half*>(sB + s * BSZ + kmaj16_off(n, k, KR)) = __float2half_rn(dg[s]);
+  }
+  if (t < D) s_moff[t] = g.hoff[g.run_of[t]] + g.loff[t];
+  if (t == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar_a) : "memory");
+  if (w == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_slot);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(dst), "r"(NCOL) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  // kind::f16: D = F32 (bit 4), A = B = F16 (formats 0), both K-major, N = KR, M = 128
+  const uint32_t idesc = (1u << 4) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  const uint32_t aS = (uint32_t)__cvta_generic_to_shared(sA), bS = (uint32_t)__cvta_generic_to_shared(sB);
+  const uint32_t L = 1u << g.lb;
+  const uint64_t* moff = s_moff + m0;
+  const uint64_t goff = g.goff[row];
+  auto tile_base = [&](uint64_t T) {
+    uint64_t b = T << g.tg_log;
+    for (int i = 0; i < g.nins; i++) b = qc_insert_zero(b, g.ins[i]);
+    return ((b | g.orval) & ~(uint64_t)(L - 1)) + goff;
+  };
+  double2 x[H];
+  uint64_t T = blockIdx.x;
+  uint64_t base = 0;
+  if (T < g.ntiles) {
+    base = tile_base(T);
+#pragma unroll
+    for (int r = 0; r < H; r++) x[r] = st[base + moff[r]];
+  }
+  uint32_t phase = 0;
+  bool ok = true;
+  for (; T < g.ntiles && ok; T += gridDim.x) {
+    // the group's scale: largest exponent over all its entries
+    int em = 0;
+#pragma unroll
+    for (int r = 0; r < H; r++) {
+      em = max(em, (__double2hiint(x[r].x) >> 20) & 0x7FF);
+      em = max(em, (__double2hiint(x[r].y) >> 20) & 0x7FF);
+    }
+    s_emax[part_of][row] = em;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TPR; i++) em = max(em, s_emax[i][row]);
+    const int E = em - 1023 - 7;                  // |x| * 2^-E < 2^8
+    const float scale = E < -126 ? 0.f : __uint_as_float((uint32_t)(127 - E) << 23);
+    // digits of this thread's entries: Re -> column m0 + r, Im -> column D + m0 + r;
+    // 16-byte stores (8 columns) where the thread has them
+#pragma unroll
+    for (int part = 0; part < 2; part++) {
+      constexpr int CW = H >= 8 ? 8 : 4;          // columns per store
+#pragma unroll
+      for (int c0 = 0; c0 < H; c0 += CW) {
+        float dg[CW][kTcDig];
+#pragma unroll
+        for (int j = 0; j < CW; j++) {
+          const double v = part == 0 ? x[c0 + j].x : x[c0 + j].y;
+          const ArC128x::ff f = ArC128x::split((uint32_t)__double2loint(v), (uint32_t)__double2hiint(v));
+          tc_digits(f.h, f.l, scale, dg[j]);
+        }
+        const int col = part * D + m0 + c0;
+#pragma unroll
+        for (int s = 0; s < kTcDig; s++) {
+          if constexpr (CW == 8)
+            *reinterpret_cast<uint4*>(sA + s * ASZ + kmaj16_off(row, col, KR)) =
+                make_uint4(pack_h2(dg[0][s], dg[1][s]), pack_h2(dg[2][s], dg[3][s]),
+                           pack_h2(dg[4][s], dg[5][s]), pack_h2(dg[6][s], dg[7][s]));
+          else
+            *reinterpret_cast<uint2*>(sA + s * ASZ + kmaj16_off(row, col, KR)) =
+                make_uint2(pack_h2(dg[0][s], dg[1][s]), pack_h2(dg[2][s], dg[3][s]));
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (t == 0) {
+      // 21 digit-matrix products, level d = sa + sb into accumulator d
+#pragma unroll
+      for (int d = 0; d < kTcLev; d++) {
+#pragma unroll
+        for (int sa = 0; sa <= d; sa++) {
+          const int sb = d - sa;
+#pragma unroll
+          for (int kk = 0; kk < KR / 16; kk++) {
+            const uint64_t ad = umma_desc(aS + sa * ASZ + kk * 256, 128, SBO);
+            const uint64_t bd = umma_desc(bS + sb * BSZ + kk * 256, 128, SBO);
+            const uint32_t acc = (sa > 0 || kk > 0) ? 1u : 0u;
+            asm volatile("{ .reg .pred q; setp.ne.b32 q, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q; }"
+                         :: "r"(tmem + (uint32_t)(d * KR)), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar_a) : "memory");
+    }
+    // prefetch the next tile while the tensor cores work
+    const uint64_t curbase = base;
+    const int Ecur = E;
+    const uint64_t Tn = T + gridDim.x;
+    if (Tn < g.ntiles) {
+      base = tile_base(Tn);
+#pragma unroll
+      for (int r = 0; r < H; r++) x[r] = st[base + moff[r]];
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; it++)
+      asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
+                   : "=r"(done) : "r"(mbar_a), "r"(phase) : "memory");
+    phase ^= 1u;
+    done = __syncthreads_and(done);   // one decision for the whole CTA (tcgen05.ld is warp-collective)
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!done) {
+      if (t == 0) atomicAdd(&g_tc_timeouts, 1);
+      ok = false;
+    } else {
+      const uint32_t lane = tmem + ((uint32_t)(32 * (w & 3)) << 16);
+      constexpr int NC = 4;
+#pragma unroll
+      for (int c = 0; c < H; c += NC) {
+        uint32_t re[kTcLev][NC], im[kTcLev][NC];
+#pragma unroll
+        for (int d = 0; d < kTcLev; d++) {
+          tmem_ld<NC>(lane + (uint32_t)(d * KR + m0 + c), re[d]);
+          tmem_ld<NC>(lane + (uint32_t)(d * KR + D + m0 + c), im[d]);
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < NC; j++) {
+          float Dr[kTcLev], Di[kTcLev];
+#pragma unroll
+          for (int d = 0; d < kTcLev; d++) { Dr[d] = __uint_as_float(re[d][j]); Di[d] = __uint_as_float(im[d][j]); }
+          const double vr = Ecur < -126 ? 0.0 : tc_scale(tc_combine(Dr), Ecur - 8);
+          const double vi = Ecur < -126 ? 0.0 : tc_scale(tc_combine(Di), Ecur - 8);
+          st[curbase + moff[c + j]] = make_double2(vr, vi);
+        }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1202,6 +1478,53 @@ int launch_fused_tc_t(qc_state* s, const qc_op& op, const GeomF& g) {
   return QC_OK;
 }
 
+template <int K>
+int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
+  constexpr int D = 1 << K, KR = 2 * D;
+  MatC128<K> U;
+  for (int i = 0; i < D * D; i++) U.u[i] = make_double2(op.U[2 * i], op.U[2 * i + 1]);
+  const size_t smem = (size_t)kTcDig * (128 * KR * 2 + KR * KR * 2);
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    QC_CUDA(cudaFuncSetAttribute(k_fused_tc128<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QC_CUDA(cudaFuncSetAttribute(k_fused_tc128<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    cudaFuncAttributes fa;
+    QC_CUDA(cudaFuncGetAttributes(&fa, k_fused_tc128<K>));
+    int dev = 0, smem_sm = 0, regs_sm = 0;
+    QC_CUDA(cudaGetDevice(&dev));
+    QC_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    QC_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+    constexpr int NT = Tc128Cfg<K>::NT;
+    const int by_regs = regs_sm / (warp_regs * (NT / 32));
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+    const int ncol = kTcLev * KR <= 128 ? 128 : (kTcLev * KR <= 256 ? 256 : 512);
+    per_sm = std::max(1, std::min(std::min(by_regs, by_smem), std::min(512 / ncol, 2048 / NT)));
+  }
+  const uint64_t cap = (uint64_t)qc_num_sms() * per_sm;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
+  k_fused_tc128<K><<<grid, Tc128Cfg<K>::NT, smem, s->stream>>>((double2*)s->ptr, g, U);
+  QC_LAUNCHED("k_fused_tc128");
+  return QC_OK;
+}
+
+// complex128 (float-float arithmetic) k = 3..5 blocks with 128-group tiles:
+// tensor cores with exact digit slices.
+int launch_fused_tc128(qc_state* s, const qc_op& op, bool* done) {
+  *done = false;
+  if (op.k < 3 || op.k > 5 || s->n - op.k - op.nc < 7) return QC_OK;
+  GeomF g;
+  size_t smem = 0;
+  if (!fused_geom(s, op, 8, g, smem) || g.tg_log != 7) return QC_OK;
+  *done = true;
+  switch (op.k) {
+    case 3: return launch_fused_tc128_t<3>(s, op, g);
+    case 4: return launch_fused_tc128_t<4>(s, op, g);
+    default: return launch_fused_tc128_t<5>(s, op, g);
+  }
+}
+
 // complex64 k = 3..5 blocks with 128-group tiles go to the tensor cores.
 int launch_fused_tc(qc_state* s, const qc_op& op, bool* done) {
   *done = false;
@@ -1426,6 +1749,12 @@ int dispatch(qc_state* s, qc_op op) {
     if constexpr (Ar::V == 4) {
       if (s->fused_tc) {
         if (int rc = launch_fused_tc(s, op, &done)) return rc;
+        if (done) return QC_OK;
+      }
+    }
+    if constexpr (std::is_same<Ar, ArC128x>::value) {
+      if (s->fused_tc) {
+        if (int rc = launch_fused_tc128(s, op, &done)) return rc;
         if (done) return QC_OK;
       }
     }
