@@ -39,6 +39,7 @@ BRICK_DEPTH = 40
 SEED_BASIS = 1000
 SEED_BRICK = 1001
 TFXY_STEPS = 10          # TFXY Trotter circuit: 10 steps = 1760 gates at n=30
+TFXY_C128_K = 5          # its fastest complex128 fusion width (measured)
 SEED_TFXY = 1003
 HBM_FALLBACK = 6800.0
 
@@ -467,7 +468,7 @@ def run_fused_case(args):
                            "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
     print(json.dumps({"case": "fused", "circuit": args.circuit, "n": n, "dtype": args.dtype, "arith": args.arith,
                       "gates": len(gates),
-                      "tensor_cores": (not args.no_tc) and args.dtype == "c64",
+                      "tensor_cores": (not args.no_tc) and (args.dtype == "c64" or args.arith == "f32x2"),
                       "by_fuse_k": res, "n_err": args.n_err, "error_vs_oracle": err,
                       "speedup_best_vs_unfused": (round(res["0"]["ms"] / min(v["ms"] for v in res.values()), 2)
                                                   if "0" in res else None)}))
@@ -573,16 +574,16 @@ def extra_measurements(q, st, stream, brick, x):
     this GPU, outside the main timed region (each reported with its config)."""
     import torch
     out = {}
-    # fused brickwork (n=30): complex128 (float-float, k=2 blocks) and complex64 (tensor cores, k=5)
+    # fused brickwork (n=30): complex128 and complex64 k=5 blocks on the tensor cores
     fused = {}
     def brick_run(state, k):
         state.set_basis(0)
         state.apply_circuit(brick, fuse_k=k)
-    brick_run(st, 2)
+    brick_run(st, 5)
     t0 = _event_ms(stream, lambda: brick_run(st, 0))
-    t2 = _event_ms(stream, lambda: brick_run(st, 2))
-    fused["c128_k2"] = {"ms": round(t2, 1), "unfused_ms": round(t0, 1), "speedup": round(t0 / t2, 2),
-                        "launches": len(q.fuse_plan(N_QUBITS, brick, 2))}
+    t5 = _event_ms(stream, lambda: brick_run(st, 5))
+    fused["c128_k5_tensor_cores"] = {"ms": round(t5, 1), "unfused_ms": round(t0, 1), "speedup": round(t0 / t5, 2),
+                                     "launches": len(q.fuse_plan(N_QUBITS, brick, 5))}
     qft = C.qft(N_QUBITS)
     def qft_run(k):
         st.set_basis(x)
@@ -634,11 +635,11 @@ def extra_measurements(q, st, stream, brick, x):
     s64.free()
     del t64
     torch.cuda.empty_cache()
-    tfxy_run(st, 2)
+    tfxy_run(st, TFXY_C128_K)
     w0 = _event_ms(stream, lambda: tfxy_run(st, 0))
-    w2 = _event_ms(stream, lambda: tfxy_run(st, 2))
-    fused["tfxy_c128_k2"] = {"ms": round(w2, 1), "unfused_ms": round(w0, 1), "speedup": round(w0 / w2, 2),
-                             "launches": len(q.fuse_plan(N_QUBITS, tfxy, 2))}
+    wk = _event_ms(stream, lambda: tfxy_run(st, TFXY_C128_K))
+    fused["tfxy_c128_k%d" % TFXY_C128_K] = {"ms": round(wk, 1), "unfused_ms": round(w0, 1), "speedup": round(w0 / wk, 2),
+                                            "launches": len(q.fuse_plan(N_QUBITS, tfxy, TFXY_C128_K))}
     out["fused"] = {"workload": "n=30: brickwork depth 40 (greedy k-qubit blocks); QFT (each H merged with its "
                                 "phase run, final SWAPs as one bit permutation); TFXY Trotter, 10 steps", **fused}
     # batched: 1024 circuits, one persistent launch vs one launch per gate
