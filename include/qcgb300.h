@@ -234,6 +234,40 @@ typedef struct {
 int qc_fuse_plan(int n, const qc_gate* gates, int ngates, int fuse_k,
                  qc_block* blocks, int max_blocks, int* nblocks);
 
+/* ---- OpenQASM 2.0 input and output ----------------------------------------
+ * The paper's library reads and writes circuits as openQASM (Sec. 3).
+ * Register qubits are numbered in declaration order: element 0 of the first
+ * qreg is qubit 0 (the most significant index bit, Definition 1).
+ *
+ * qc_qasm_parse: read an OpenQASM 2.0 program (text, NUL-terminated host
+ * string) into a program object owned by the caller (free it with
+ * qc_program_free).  Reads qreg/creg, gate definitions (expanded), parameter
+ * expressions (numbers, pi, + - * / ^, sin cos tan exp ln sqrt), register
+ * broadcasting and the gates U u3 u u2 u1 p CX cx id u0 x y z h s sdg t tdg sx
+ * sxdg rx ry rz cy cz ch swap ccx cswap crx cry crz cu1 cp cu3 cu rzz rxx
+ * (U(t,f,l) = [[cos t/2, -e^{il} sin t/2], [e^{if} sin t/2, e^{i(f+l)} cos t/2]]).
+ * measure and barrier are skipped and counted; reset, if and opaque return
+ * QC_ERR_UNSUPPORTED; syntax errors, unknown gates and registers, out-of-range
+ * indices return QC_ERR_ARG with the line in qc_last_error(). */
+typedef struct qc_program qc_program;
+int qc_qasm_parse(const char* text, qc_program** out);
+/* Number of qubits, of gates, and of skipped measure/barrier statements. */
+int qc_program_info(const qc_program* p, int* nqubits, int* ngates, int* nignored);
+/* The program's gate records (matrices owned by the program), ready for
+ * qc_apply_circuit; valid until qc_program_free.  NULL for an empty program. */
+const qc_gate* qc_program_gates(const qc_program* p);
+int qc_program_free(qc_program* p);
+
+/* qc_qasm_write: the gate list as an OpenQASM 2.0 program over one register
+ * q[n].  Named gates map to their qelib1 names (controlled X/Y/Z/H, P, RX,
+ * RY, RZ with one control, ccx, cswap); control states 0 are conjugated with
+ * x; a 1-qubit matrix becomes u3 (its global phase, unobservable, dropped) and
+ * a singly controlled one cu3 followed by u1 on the control (exact).  Other
+ * gates (k >= 2 matrices, more controls) return QC_ERR_UNSUPPORTED.  Writes at
+ * most cap bytes including the NUL to buf (buf may be NULL to query *len, the
+ * length without the NUL). */
+int qc_qasm_write(int n, const qc_gate* gates, int ngates, char* buf, size_t cap, size_t* len);
+
 /* ---- batches of circuits -----------------------------------------------------
  * Many independent circuits of different sizes and depths run in one
  * persistent kernel launch (optionally captured in a CUDA graph and replayed).

@@ -103,6 +103,11 @@ def _load():
         "qc_expect": [P, ctypes.POINTER(qc_pauli_sum), DP],
         "qc_expect_noalloc": [P, ctypes.POINTER(qc_pauli_sum), DP],
         "qc_expect_passes": [I, I, ctypes.POINTER(qc_pauli_sum), IP],
+        "qc_qasm_parse": [ctypes.c_char_p, ctypes.POINTER(P)],
+        "qc_program_info": [P, IP, IP, IP],
+        "qc_program_free": [P],
+        "qc_qasm_write": [I, ctypes.POINTER(qc_gate), I, ctypes.c_char_p, ctypes.c_size_t,
+                          ctypes.POINTER(ctypes.c_size_t)],
         "qc_fuse_plan": [I, ctypes.POINTER(qc_gate), I, I, ctypes.POINTER(qc_block), I, IP],
         "qc_adjoint_grad": [I, ctypes.POINTER(qc_gate), I, DP, I, ctypes.POINTER(qc_pauli_sum), DP, DP,
                             ctypes.POINTER(qc_grad_opts)],
@@ -335,6 +340,52 @@ def expect_passes(n: int, dtype: int, hamiltonian) -> int:
     _check(lib.qc_expect_passes(n, dtype, ctypes.byref(rec), ctypes.byref(out)))
     del keep
     return out.value
+
+
+_KIND_NAME = {1: "H", 2: "X", 3: "Y", 4: "Z", 5: "S", 6: "SDG", 7: "T", 8: "TDG", 9: "P", 10: "RX", 11: "RY",
+              12: "RZ", 13: "SWAP"}
+
+
+def qasm_parse(text: str):
+    """OpenQASM 2.0 text -> (nqubits, [Gate, ...], skipped measure/barrier count)."""
+    from .circuits import Gate
+    prog = ctypes.c_void_p()
+    _check(lib.qc_qasm_parse(text.encode(), ctypes.byref(prog)))
+    try:
+        n, ng, ni = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib.qc_program_info(prog, ctypes.byref(n), ctypes.byref(ng), ctypes.byref(ni)))
+        fn = lib.qc_program_gates
+        fn.restype = ctypes.POINTER(qc_gate)
+        fn.argtypes = [ctypes.c_void_p]
+        recs = fn(prog)
+        gates = []
+        for i in range(ng.value):
+            r = recs[i]
+            qubits = tuple(r.qubits[:r.nq])
+            controls = tuple(r.controls[:r.nc])
+            cstates = tuple(r.cstates[:r.nc])
+            if r.kind == 0:
+                d = 1 << r.nq
+                m = np.array([complex(r.matrix[2 * j], r.matrix[2 * j + 1]) for j in range(d * d)]).reshape(d, d)
+                name = "U" if r.nq == 1 else ("U4" if r.nq == 2 else "UK")
+                gates.append(Gate(name, qubits, controls=controls, cstates=cstates, matrix=m))
+            else:
+                gates.append(Gate(_KIND_NAME[r.kind], qubits, controls=controls, cstates=cstates,
+                                  theta=float(r.theta)))
+        return n.value, gates, ni.value
+    finally:
+        lib.qc_program_free(prog)
+
+
+def qasm_write(n: int, gates) -> str:
+    """Gate list -> OpenQASM 2.0 text over q[n]."""
+    arr, keep = gate_records(gates)
+    ln = ctypes.c_size_t(0)
+    _check(lib.qc_qasm_write(n, arr, len(gates), None, 0, ctypes.byref(ln)))
+    buf = ctypes.create_string_buffer(ln.value + 1)
+    _check(lib.qc_qasm_write(n, arr, len(gates), buf, ln.value + 1, ctypes.byref(ln)))
+    del keep
+    return buf.value.decode()
 
 
 def fuse_plan(n: int, gates, fuse_k: int):

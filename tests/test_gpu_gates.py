@@ -576,3 +576,19 @@ def test_tfxy_n28_then_inverse_returns_basis_state(q, dtype, fuse_k):
     st.free()
     del t
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------------ OpenQASM programs
+@pytest.mark.parametrize("mode", MODES)
+def test_qasm_program_through_the_library(q, mode):
+    """A program written as OpenQASM 2.0 (QFT + two TFXY Trotter steps, n=12),
+    read back and applied gate by gate and fused, against the oracle on the
+    original gate list."""
+    n = 12
+    gates = C.qft(n) + C.tfxy_trotter(n, 2, seed=3)
+    m, back, _ = q.qasm_parse(q.qasm_write(n, gates))
+    assert m == n and len(back) == len(gates)
+    phi = C.random_state(n, 12)
+    ref = O.run_circuit(n, gates, phi)
+    for k in (0, 4):
+        assert maxerr(gpu_run(q, n, back, mode, psi0=phi, fuse_k=k), ref) <= TOL[mode]
