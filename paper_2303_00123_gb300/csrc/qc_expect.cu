@@ -491,8 +491,14 @@ k_pauli_tile(const unsigned char* __restrict__ psi, const __grid_constant__ TPas
     gtab[c] = g;
   }
   const uint64_t zz = P.ntiles >> 63;   // 0 (ntiles <= 2^36), opaque to the compiler
-  float th = 0.f, tl = 0.f;
+  // A tile's terms are summed in float-float (th, tl); each tile's sum then
+  // joins a per-thread FP64 total.  (Carrying one float-float pair across
+  // all of a thread's tiles -- hundreds of tiles and tens of thousands of
+  // additions at 30 qubits -- let its unnormalised low word lose precision:
+  // 3e-10 off a closed form.)
+  double tot = 0.0;
   for (uint64_t tix = blockIdx.x; tix < P.ntiles; tix += gridDim.x) {
+    float th = 0.f, tl = 0.f;
     uint64_t base = tix << P.m;
     for (int i = 0; i < P.h; i++) base = qc_insert_zero(base, P.piv[i]);
     __syncthreads();                 // previous tile consumed, gtab written
@@ -516,9 +522,10 @@ k_pauli_tile(const unsigned char* __restrict__ psi, const __grid_constant__ TPas
       __syncthreads();               // pair groups done reading the tile
       tile_diag<C128>(tile, gtab, P, base, zz, th, tl);
     }
+    tot += ArC128x::f2d(th) + ArC128x::f2d(tl);   // exact conversions (integer operations)
   }
-  const double tot = block_sum((double)th + (double)tl);
-  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+  const double bs = block_sum(tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
 }
 
 // ---- host planning --------------------------------------------------------

@@ -164,3 +164,24 @@ def test_repeated_and_reordered_terms(q, dtype):
          (0.7, [("Z", 1), ("X", 9), ("Z", 12)]), (0.7, [("Z", 12), ("X", 9), ("Z", 1)]),
          (1.1, [("Y", 0), ("Y", 12)]), (-1.1, [("Y", 12), ("Y", 0)]), (0.4, [("Z", 5)]), (0.4, [("Z", 5)])]
     check(q, n, dtype, H, seed=77)
+
+
+def test_qft_state_closed_form_n30(q):
+    """n=30 complex128, the QFT of a basis state |x> (a product state):
+    |psi_y|^2 = 1/N makes every ZZ term vanish and <X_q> = cos(2 pi x 2^b / N),
+    b = n-1-q, so the TFIM energy is -sum_q cos(2 pi x 2^b / N) -- a reference
+    at full size independent of the oracle, sensitive to how the 2^30-term
+    reduction accumulates."""
+    import torch
+    n = 30
+    x = 123456789 % (1 << n)
+    t = torch.zeros(1 << n, dtype=torch.complex128, device="cuda")
+    st = q.State.from_tensor(t)
+    st.set_basis(x)
+    st.apply_circuit(C.qft(n), fuse_k=2)
+    ref = -sum(math.cos(2 * math.pi * ((x << (n - 1 - qq)) % (1 << n)) / (1 << n)) for qq in range(n))
+    got = st.expect(C.tfim(n, 1.0))
+    st.free()
+    del t
+    torch.cuda.empty_cache()
+    assert abs(got - ref) <= 1e-12 * n
