@@ -547,14 +547,14 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
 // entry is written as six balanced base-2^9 digits, |digit| <= 256, which
 // fp16 holds exactly:
 //   x = 2^E_g * sum_s a_s 2^(-9 s)   (E_g from the largest entry of group g),
-//   r = 2^-8  * sum_t b_t 2^(-9 t)   (|r| <= 1 for a unitary),
+//   r = 2^(eu-8) * sum_t b_t 2^(-9 t)  (|r| < 2^eu; eu = 1 for a unitary),
 // and the products of digit matrices are summed by level d = s + t (d <= 5,
 // 21 products) into six FP32 accumulators in tensor memory.  A digit product
 // is at most 2^16 and K <= 64, so levels 0..3 (at most 4 products each, sums
 // below 2^24) are exact integer sums; levels 4 and 5 may round, 2^-60 below
 // the group's scale.  The epilogue recombines sum_d 2^(-9 d) D_d in
 // float-float (powers of two are exact), converts to double and applies
-// 2^(E_g - 8) to the exponent field.  Error: about 2^-47 of the group's
+// 2^(E_g - 8 + eu) to the exponent field.  Error: about 2^-47 of the group's
 // largest entry (the float-float split of the input), like the complex128
 // CUDA-core arithmetic.  Entries below 2^-119 of a group are flushed to zero.
 template <int K>
@@ -633,7 +633,8 @@ template <int K> struct Tc128Cfg {
 
 template <int K>
 __global__ void __launch_bounds__(Tc128Cfg<K>::NT, 1)
-k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC128<K> U) {
+k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC128<K> U,
+              int eu) {
   constexpr int D = 1 << K;
   constexpr int TPR = Tc128Cfg<K>::TPR, NT = Tc128Cfg<K>::NT;
   constexpr int H = D / TPR;                      // members per thread
@@ -655,14 +656,15 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
   const int part_of = t >> 7;                     // which slice of the row's members
   const int m0 = part_of * H;
   const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
-  // B digits: B[n][k] = R[n][k] * 2^8, R = [[Ur, -Ui], [Ui, Ur]]
+  // B digits: B[n][k] = R[n][k] * 2^(8 - eu), R = [[Ur, -Ui], [Ui, Ur]], |R| < 2^eu
+  const float uscale = __uint_as_float((uint32_t)(127 + 8 - eu) << 23);
   for (int i = t; i < KR * KR; i += NT) {
     const int n = i / KR, k = i % KR;
     const double2 u = U.u[(n % D) * D + (k % D)];
     const double v = n < D ? (k < D ? u.x : -u.y) : (k < D ? u.y : u.x);
     const ArC128x::ff f = ArC128x::split((uint32_t)__double2loint(v), (uint32_t)__double2hiint(v));
     float dg[kTcDig];
-    tc_digits(f.h, f.l, 256.f, dg);
+    tc_digits(f.h, f.l, uscale, dg);
 #pragma unroll
     for (int s = 0; s < kTcDig; s++)
       *reinterpret_cast<__half*>(sB + s * BSZ + kmaj16_off(n, k, KR)) = __float2half_rn(dg[s]);
@@ -800,8 +802,8 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
           float Dr[kTcLev], Di[kTcLev];
 #pragma unroll
           for (int d = 0; d < kTcLev; d++) { Dr[d] = __uint_as_float(re[d][j]); Di[d] = __uint_as_float(im[d][j]); }
-          const double vr = Ecur < -126 ? 0.0 : tc_scale(tc_combine(Dr), Ecur - 8);
-          const double vi = Ecur < -126 ? 0.0 : tc_scale(tc_combine(Di), Ecur - 8);
+          const double vr = Ecur < -126 ? 0.0 : tc_scale(tc_combine(Dr), Ecur - 8 + eu);
+          const double vi = Ecur < -126 ? 0.0 : tc_scale(tc_combine(Di), Ecur - 8 + eu);
           st[curbase + moff[c + j]] = make_double2(vr, vi);
         }
       }
@@ -1482,7 +1484,15 @@ template <int K>
 int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
   constexpr int D = 1 << K, KR = 2 * D;
   MatC128<K> U;
-  for (int i = 0; i < D * D; i++) U.u[i] = make_double2(op.U[2 * i], op.U[2 * i + 1]);
+  double umax = 0.0;
+  for (int i = 0; i < D * D; i++) {
+    U.u[i] = make_double2(op.U[2 * i], op.U[2 * i + 1]);
+    umax = std::max(umax, std::max(std::fabs(op.U[2 * i]), std::fabs(op.U[2 * i + 1])));
+  }
+  // digits of the matrix scaled by 2^(8 - eu) with |entries| < 2^eu (eu = 1 for a unitary
+  // with an entry of modulus 1; any matrix is allowed)
+  const int eu = umax > 0.0 ? std::ilogb(umax) + 1 : 0;
+  if (eu > 100 || eu < -100) return qc_fail(QC_ERR_ARG, "matrix entries out of range for the tensor-core path");
   const size_t smem = (size_t)kTcDig * (128 * KR * 2 + KR * KR * 2);
   static int per_sm = 0;
   if (per_sm == 0) {
@@ -1504,7 +1514,7 @@ int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
   }
   const uint64_t cap = (uint64_t)qc_num_sms() * per_sm;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
-  k_fused_tc128<K><<<grid, Tc128Cfg<K>::NT, smem, s->stream>>>((double2*)s->ptr, g, U);
+  k_fused_tc128<K><<<grid, Tc128Cfg<K>::NT, smem, s->stream>>>((double2*)s->ptr, g, U, eu);
   QC_LAUNCHED("k_fused_tc128");
   return QC_OK;
 }

@@ -87,3 +87,22 @@ def test_fused_brickwork_and_tfxy_n16(q):
         ref = O.run_circuit(n, gates, phi)
         for k in (3, 4, 5):
             assert np.max(np.abs(run(q, n, gates, phi, fuse_k=k) - ref)) <= 1e-12
+
+
+def test_non_unitary_block_through_the_kq_entry_point(q):
+    """qc_apply_kq takes any matrix: entries up to ~40 (the digit scale of the
+    matrix follows its largest entry) and a tiny-norm matrix."""
+    n = 12
+    rng = np.random.default_rng(55)
+    phi = C.random_state(n, 5)
+    for scale in (37.0, 3e-9):
+        M = scale * (rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32)))
+        g = [Gate("UK", (1, 4, 6, 9, 11), matrix=M)]
+        st = q.State(n, q.C128)
+        st.set_arith(q.ARITH_F32X2)
+        st.from_numpy(phi)
+        st.apply_kq(M, [1, 4, 6, 9, 11])
+        got = st.to_numpy()
+        st.free()
+        ref = O.run_circuit(n, g, phi)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
