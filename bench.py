@@ -179,6 +179,14 @@ def cpu_oracle_sample(n_gates_each=6):
                       "(%d gates, %.1f s)" % (n_gates_each, N_QUBITS, len(sample), dt)}
 
 
+def workload_config(args, world, gates_per_step):
+    """The `config` both arms report: the same workload, whichever arm runs it."""
+    return {"workload": "n=30 complex128 QFT (seeded basis state) + brickwork depth 40 (Haar U(2) "
+                        "layers + CNOT pairs), gate by gate", "n": N_QUBITS, "gates_per_step": gates_per_step,
+            "fuse_k": args.fuse, "arith": args.arith, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (17.2 GB state vs 129 MB)"}
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -275,10 +283,7 @@ def run_gpu(args):
         "value": round(value, 3), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed / args.steps * 1e3, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128-" + args.arith, "data": "synthetic",
-        "config": {"workload": "n=30 complex128 QFT (seeded basis state) + brickwork depth 40 (Haar U(2) "
-                               "layers + CNOT pairs), gate by gate", "n": n, "gates_per_step": gates_per_step,
-                   "fuse_k": args.fuse, "arith": args.arith, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (17.2 GB state vs 129 MB)"},
+        "config": workload_config(args, world, gates_per_step),
         "gpu_launches": launches,
         "roofline": roof,
         "e2e": e2e,
@@ -724,7 +729,7 @@ def run_reference(args):
         "value": round(value, 4), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "n=30 complex128 QFT + brickwork sample, FP64 CPU oracle", "n": N_QUBITS},
+        "config": workload_config(args, world, len(qft) + len(brick)),
         "cpu_baseline": cpu, "e2e": {"value": round(value, 4), "unit": "gates/s", "h2d_bytes_per_step": 0,
                                      "d2h_bytes_per_step": 0}}))
 
