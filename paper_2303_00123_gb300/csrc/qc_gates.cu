@@ -544,57 +544,117 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
 // complex128 dense k-qubit block (k = 3..5) on the tensor cores, with exact
 // integer slices (the error-free splitting idea of Ozaki et al.): the same
 // GEMM as k_fused_tc (128 groups x 2D reals times R^T), but every operand
-// entry is written as six balanced base-2^9 digits, |digit| <= 256, which
-// fp16 holds exactly:
-//   x = 2^E_g * sum_s a_s 2^(-9 s)   (E_g from the largest entry of group g),
-//   r = 2^(eu-8) * sum_t b_t 2^(-9 t)  (|r| < 2^eu; eu = 1 for a unitary),
-// and the products of digit matrices are summed by level d = s + t (d <= 5,
-// 21 products) into six FP32 accumulators in tensor memory.  A digit product
-// is at most 2^16 and K <= 64, so levels 0..3 (at most 4 products each, sums
-// below 2^24) are exact integer sums; levels 4 and 5 may round, 2^-60 below
-// the group's scale.  The epilogue recombines sum_d 2^(-9 d) D_d in
-// float-float (powers of two are exact), converts to double and applies
-// 2^(E_g - 8 + eu) to the exponent field.  Error: about 2^-47 of the group's
-// largest entry (the float-float split of the input), like the complex128
-// CUDA-core arithmetic.  Entries below 2^-119 of a group are flushed to zero.
+// entry is written as balanced base-2^8 digits that fp16 holds exactly.
+//   State (A): each entry, aligned to the largest exponent E of its group
+//   (2^E <= max|x| < 2^(E+1)), is rounded to an integer q < 2^48 in units of
+//   2^(E-47) and written as q = sum_s a_s 2^(8(5-s)), a_0 in [0, 256],
+//   a_1..a_5 in [-128, 127], times the entry's sign; the digits are bytes of
+//   q + 0x8080808080 read by integer operations.
+//   Matrix (B): r 2^(7-eu) (|r| < 2^eu) = sum_t b_t 2^(-8t), t = 0..6,
+//   |b_t| <= 128 (balanced: each step removes the nearest integer).
+// Products of digit matrices are summed by level d = s + t <= 6 (27 of
+// them) into seven FP32 accumulators in tensor memory.  A digit product is at
+// most 2^15 and K <= 64, so every level sum stays below 2^23: exact.  Levels
+// 0..2 are at most 2^22 and become integers by one float addition, levels 3
+// and 4 by two; D5 + D6/256 is rounded the same way.  The epilogue assembles
+// sum_{d<=4} D_d 2^(8(5-d)) + round(D5 + D6/256) as a 64-bit integer,
+// converts it to double once and adds the scale to the exponent field.
+// Error: at most half a unit of 2^(E-47) per state entry (the rounding of q)
+// and about 2^-54 of the group's largest entry from the matrix digits and the
+// dropped levels d >= 7.  Entries below 2^-48 of their group's largest one
+// contribute nothing; groups whose largest entry is below 2^-959 give zero.
 template <int K>
 struct MatC128 { double2 u[(1 << K) * (1 << K)]; };
 
-constexpr int kTcDig = 6;                         // digits per operand entry
-constexpr int kTcLev = 6;                         // accumulator levels d = s + t <= 5
+constexpr int kTcA = 6;                           // state digits
+constexpr int kTcB = 7;                           // matrix digits
+constexpr int kTcLev = 7;                         // accumulator levels d = s + t <= 6
 
-__device__ __forceinline__ float tc_rnd(float x) {  // nearest integer of |x| < 2^22
-  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+// x >> s for any s (PTX clamps shift amounts above 32: the result is 0)
+__device__ __forceinline__ uint32_t shr_clamp(uint32_t x, uint32_t s) {
+  uint32_t r;
+  asm("shr.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(s));
+  return r;
 }
 
-// Digits of (h + l) * scale, h + l a float-float value, |h * scale| <= 256:
-// each step removes the nearest integer and scales the remainder by 2^9.  The
-// lo word joins when the hi word's bits are used up; it is added to the
-// remainder only where the sum is exact, and only steers the digit choice
-// before that, so every digit stays within [-256, 256].
-__device__ __forceinline__ void tc_digits(float h, float l, float scale, float* d) {
-  const float hs = __fmul_rn(h, scale);
-  float ls = __fmul_rn(l, scale);
-  d[0] = tc_rnd(hs);
-  float r = __fmul_rn(__fsub_rn(hs, d[0]), 512.f);      // exact
-  ls = __fmul_rn(ls, 512.f);
-  d[1] = tc_rnd(__fadd_rn(r, ls));
-  float rh = __fmul_rn(__fsub_rn(r, d[1]), 512.f);      // exact: a multiple of 4
-  ls = __fmul_rn(ls, 512.f);
-  d[2] = tc_rnd(__fadd_rn(rh, ls));
-  r = __fadd_rn(__fsub_rn(rh, d[2]), ls);               // small integer + ls: exact
-#pragma unroll
-  for (int i = 3; i < kTcDig; i++) {
-    r = __fmul_rn(r, 512.f);
-    d[i] = tc_rnd(r);
-    r = __fsub_rn(r, d[i]);
+// q + 0x8080808080 as (high word, low word), q = round(m / 2^(emax5 - e)) for the
+// entry with high word hi, low word lo (m its 53-bit mantissa, e its exponent
+// field), emax5 = the group's largest exponent field + 5.
+struct TcQ { uint32_t h, l; };
+__device__ __forceinline__ TcQ tc_window(uint32_t hi, uint32_t lo, int emax5) {
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+  const uint32_t s1 = (uint32_t)(emax5 - e - 1);  // >= 4
+  const uint32_t tl = s1 < 32u ? __funnelshift_r(lo, mh, s1) : shr_clamp(mh, s1 - 32u);
+  const uint32_t th = shr_clamp(mh, s1);
+  // (t + 1) >> 1 rounds half up; adding 2 * 0x8080808080 before the shift adds the digit offset
+  const uint64_t t = (((uint64_t)th << 32) | tl) + (1ull + 2ull * 0x8080808080ull);
+  return {(uint32_t)(t >> 33), (uint32_t)(t >> 1)};
+}
+
+// fp16x2 digits from two byte lanes: (w & 0x00FF00FF) | k is +-(1024 + byte)
+// per half (k carries the signs); subtracting t = +-(1024 or 1152) leaves the
+// signed digit, exactly.
+__device__ __forceinline__ uint32_t tc_dig2(uint32_t w, uint32_t k, uint32_t t) {
+  const uint32_t v = (w & 0x00FF00FFu) | k;
+  uint32_t r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(t));
+  return r;
+}
+
+// the six fp16x2 words (digit s of entries a and b) for two adjacent columns
+__device__ __forceinline__ void tc_digit_words(TcQ qa, TcQ qb, uint32_t hia, uint32_t hib, uint32_t* w) {
+  const uint32_t k = ((hia >> 16) & 0x8000u) | (hib & 0x80000000u) | 0x64006400u;
+  const uint32_t t1 = k | 0x00800080u;            // +-1152: bytes hold digit + 128
+  uint32_t v0 = __byte_perm(qa.h, qb.h, 0x6521) | k;   // a_0 = q' >> 40 (9 bits)
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(w[0]) : "r"(v0), "r"(k));
+  w[1] = tc_dig2(__byte_perm(qa.h, qb.h, 0x4400), k, t1);
+  w[2] = tc_dig2(__byte_perm(qa.l, qb.l, 0x7733), k, t1);
+  w[3] = tc_dig2(__byte_perm(qa.l, qb.l, 0x6622), k, t1);
+  w[4] = tc_dig2(__byte_perm(qa.l, qb.l, 0x5511), k, t1);
+  w[5] = tc_dig2(__byte_perm(qa.l, qb.l, 0x4400), k, t1);
+}
+
+// Nearest integer of a float |x| <= 2^22 by one addition (the bits of
+// x + 1.5 * 2^23, i.e. the integer plus 0x4B400000).
+__device__ __forceinline__ uint32_t tc_int22(float x) { return (uint32_t)__float_as_int(__fadd_rn(x, 12582912.f)); }
+
+// sum_d D_d 2^(8(5-d)) (levels 0..6 of one output; integer sums, |D_d| < 2^23)
+// rounded to a multiple of 2^sh, as a double times 2^scale; 0 when flush.
+// Levels 0..2 (|D| <= 2^22) convert by one addition each; levels 3, 4 and the
+// tail D5 + D6/256 too when every level is at most 2^22 (SMALL: K <= 32 terms),
+// else they are rounded to even integers by adding 1.5 * 2^24 and each
+// remainder (-1, 0 or 1, exact) moves into the next level's float.  The total
+// is a 64-bit integer; shifted right by sh (|total| <= 2^(51 + sh), chosen by
+// the host from the matrix) it sits in the mantissa of 1.5 * 2^52 + total,
+// so one double subtraction converts it exactly.
+template <bool SMALL>
+__device__ __forceinline__ double tc_assemble(const float* D, int sh, long long rnd, int scale, bool flush) {
+  constexpr uint32_t C1 = 0x4B400000u;            // bits of 1.5 * 2^23
+  const uint32_t b0 = tc_int22(D[0]), b1 = tc_int22(D[1]), b2 = tc_int22(D[2]);
+  int Q, R;
+  if constexpr (SMALL) {
+    const uint32_t b3 = tc_int22(D[3]), b4 = tc_int22(D[4]);
+    const uint32_t b5 = tc_int22(__fmaf_rn(D[6], 1.f / 256.f, D[5]));
+    Q = (int)((b2 - C1) * 256u + (b3 - C1));
+    R = (int)((b4 - C1) * 256u + (b5 - C1));
+  } else {
+    constexpr float M2 = 25165824.f;              // 1.5 * 2^24; bits(r) - 0x4BC00000 is half the even integer
+    const float r3 = __fadd_rn(D[3], M2);
+    const float e3 = __fsub_rn(D[3], __fsub_rn(r3, M2));
+    const float d4 = __fmaf_rn(e3, 256.f, D[4]);
+    const float r4 = __fadd_rn(d4, M2);
+    const float e4 = __fsub_rn(d4, __fsub_rn(r4, M2));
+    const float r5 = __fadd_rn(__fmaf_rn(e4, 256.f, __fmaf_rn(D[6], 1.f / 256.f, D[5])), M2);
+    Q = (int)((b2 - C1) * 256u + ((uint32_t)__float_as_int(r3) - 0x4BC00000u) * 2u);
+    R = (int)(((uint32_t)__float_as_int(r4) - 0x4BC00000u) * 512u + ((uint32_t)__float_as_int(r5) - 0x4BC00000u) * 2u);
   }
-}
-
-__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {   // lo -> low half
-  uint32_t v;
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(v) : "f"(hi), "f"(lo));
-  return v;
+  // |P| < 2^30, |Q|, |R| < 2^31 (unsigned arithmetic: the offsets wrap)
+  const int P = (int)(b0 * 256u + b1 - C1 * 257u);
+  const long long tr = ((long long)P * 4294967296ll + (long long)Q * 65536 + R + rnd) >> sh;
+  if (flush || tr == 0) return 0.0;
+  const double y = __longlong_as_double(tr + 0x4338000000000000ll) - 6755399441055744.0;
+  return __hiloint2double(__double2hiint(y) + scale * (1 << 20), __double2loint(y));
 }
 
 // byte offset of element (row, col) in a K-major no-swizzle fp16 operand with KR columns
@@ -602,39 +662,18 @@ __device__ __forceinline__ uint32_t kmaj16_off(int row, int col, int KR) {
   return (row >> 3) * (KR >> 3) * 128 + (col >> 3) * 128 + (row & 7) * 16 + (col & 7) * 2;
 }
 
-// sum_d 2^(-9 d) D_d in float-float (Horner from the smallest level), as a double
-__device__ __forceinline__ double tc_combine(const float* D) {
-  float ah = D[kTcLev - 1], al = 0.f;
-#pragma unroll
-  for (int d = kTcLev - 2; d >= 0; d--) {
-    ah = __fmul_rn(ah, 1.f / 512.f);
-    al = __fmul_rn(al, 1.f / 512.f);
-    const float s = __fadd_rn(D[d], ah);
-    const float z = __fsub_rn(s, D[d]);
-    const float e = __fadd_rn(__fsub_rn(D[d], __fsub_rn(s, z)), __fsub_rn(ah, z));
-    ah = s;
-    al = __fadd_rn(al, e);
-  }
-  return ArC128x::f2d(ah) + ArC128x::f2d(al);
-}
-
-// x * 2^e for a double x that stays normal (exponent field arithmetic); 0 stays 0
-__device__ __forceinline__ double tc_scale(double x, int e) {
-  if (x == 0.0) return 0.0;
-  return __hiloint2double(__double2hiint(x) + e * (1 << 20), __double2loint(x));
-}
-
 // Threads per CTA: two per accumulator row (four per row, for twice the
-// warps, measured slower; so did rolling the phases' outer loops).
+// warps, measured slower).
 template <int K> struct Tc128Cfg {
   static constexpr int TPR = 2;                   // threads per row (group)
   static constexpr int NT = 128 * TPR;
+  static constexpr int MINB = K <= 4 ? 2 : 1;     // CTAs per SM (k <= 4: 2 x 256 TMEM columns, 2 x 62 KB)
 };
 
 template <int K>
-__global__ void __launch_bounds__(Tc128Cfg<K>::NT, 1)
+__global__ void __launch_bounds__(Tc128Cfg<K>::NT, Tc128Cfg<K>::MINB)
 k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC128<K> U,
-              int eu) {
+              int eu, int sh) {
   constexpr int D = 1 << K;
   constexpr int TPR = Tc128Cfg<K>::TPR, NT = Tc128Cfg<K>::NT;
   constexpr int H = D / TPR;                      // members per thread
@@ -645,7 +684,7 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
   static_assert(H % 4 == 0, "four columns per store at least");
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* sA = smem_tc;                    // [digit][128 x KR] fp16
-  unsigned char* sB = sA + kTcDig * ASZ;          // [digit][KR x KR] fp16, row n = output n
+  unsigned char* sB = sA + kTcA * ASZ;            // [digit][KR x KR] fp16, row n = output n
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ uint64_t s_moff[D];
@@ -656,18 +695,18 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
   const int part_of = t >> 7;                     // which slice of the row's members
   const int m0 = part_of * H;
   const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
-  // B digits: B[n][k] = R[n][k] * 2^(8 - eu), R = [[Ur, -Ui], [Ui, Ur]], |R| < 2^eu
-  const float uscale = __uint_as_float((uint32_t)(127 + 8 - eu) << 23);
+  // B digits: B[n][k] = R[n][k] 2^(7 - eu), R = [[Ur, -Ui], [Ui, Ur]], |R| < 2^eu
+  const double uscale = __hiloint2double((1023 + 7 - eu) << 20, 0);
   for (int i = t; i < KR * KR; i += NT) {
     const int n = i / KR, k = i % KR;
     const double2 u = U.u[(n % D) * D + (k % D)];
-    const double v = n < D ? (k < D ? u.x : -u.y) : (k < D ? u.y : u.x);
-    const ArC128x::ff f = ArC128x::split((uint32_t)__double2loint(v), (uint32_t)__double2hiint(v));
-    float dg[kTcDig];
-    tc_digits(f.h, f.l, uscale, dg);
+    double r = (n < D ? (k < D ? u.x : -u.y) : (k < D ? u.y : u.x)) * uscale;
 #pragma unroll
-    for (int s = 0; s < kTcDig; s++)
-      *reinterpret_cast<__half*>(sB + s * BSZ + kmaj16_off(n, k, KR)) = __float2half_rn(dg[s]);
+    for (int s = 0; s < kTcB; s++) {
+      const double b = rint(r);
+      *reinterpret_cast<__half*>(sB + s * BSZ + kmaj16_off(n, k, KR)) = __float2half_rn((float)b);
+      r = (r - b) * 256.0;
+    }
   }
   if (t < D) s_moff[t] = g.hoff[g.run_of[t]] + g.loff[t];
   if (t == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar_a) : "memory");
@@ -684,6 +723,7 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
   // kind::f16: D = F32 (bit 4), A = B = F16 (formats 0), both K-major, N = KR, M = 128
   const uint32_t idesc = (1u << 4) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   const uint32_t aS = (uint32_t)__cvta_generic_to_shared(sA), bS = (uint32_t)__cvta_generic_to_shared(sB);
+  const long long rnd = sh > 0 ? 1ll << (sh - 1) : 0ll;   // rounds the total to a multiple of 2^sh
   const uint32_t L = 1u << g.lb;
   const uint64_t* moff = s_moff + m0;
   const uint64_t goff = g.goff[row];
@@ -692,126 +732,141 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
     for (int i = 0; i < g.nins; i++) b = qc_insert_zero(b, g.ins[i]);
     return ((b | g.orval) & ~(uint64_t)(L - 1)) + goff;
   };
-  double2 x[H];
-  uint64_t T = blockIdx.x;
-  uint64_t base = 0;
-  if (T < g.ntiles) {
-    base = tile_base(T);
-#pragma unroll
-    for (int r = 0; r < H; r++) x[r] = st[base + moff[r]];
-  }
+  // bounded wait for the MMAs' completion; one decision for the CTA
   uint32_t phase = 0;
-  bool ok = true;
-  for (; T < g.ntiles && ok; T += gridDim.x) {
-    // the group's scale: largest exponent over all its entries
+  auto mma_wait = [&]() {
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; it++)
+      asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
+                   : "=r"(done) : "r"(mbar_a), "r"(phase) : "memory");
+    done = __syncthreads_and(done);   // tcgen05.ld is warp-collective
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (done) phase ^= 1u;
+    else if (t == 0) atomicAdd(&g_tc_timeouts, 1);
+    return done != 0;
+  };
+  // accumulators -> doubles of the tile at obase
+  auto epilogue = [&](uint64_t obase, int scale, bool flush) {
+    const uint32_t lane = tmem + ((uint32_t)(32 * (w & 3)) << 16);
+    constexpr int NC = 4;
+#pragma unroll
+    for (int c = 0; c < H; c += NC) {
+      uint32_t re[kTcLev][NC], im[kTcLev][NC];
+#pragma unroll
+      for (int d = 0; d < kTcLev; d++) {
+        tmem_ld<NC>(lane + (uint32_t)(d * KR + m0 + c), re[d]);
+        tmem_ld<NC>(lane + (uint32_t)(d * KR + D + m0 + c), im[d]);
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < NC; j++) {
+        float Dr[kTcLev], Di[kTcLev];
+#pragma unroll
+        for (int d = 0; d < kTcLev; d++) { Dr[d] = __uint_as_float(re[d][j]); Di[d] = __uint_as_float(im[d][j]); }
+        st[obase + moff[c + j]] = make_double2(tc_assemble<(KR <= 32)>(Dr, sh, rnd, scale, flush),
+                                                 tc_assemble<(KR <= 32)>(Di, sh, rnd, scale, flush));
+      }
+    }
+  };
+  // 27 digit-matrix products, level d = sa + sb into accumulator d.  Descriptors:
+  // the start address (>> 4) is the low 14 bits and every operand lies below
+  // 2^18 bytes, so an offset is one 32-bit addition to the low word.
+  auto issue_mma = [&]() {
+    const uint64_t adesc0 = umma_desc(aS, 128, SBO), bdesc0 = umma_desc(bS, 128, SBO);
+    const uint32_t alo = (uint32_t)adesc0, ahi = (uint32_t)(adesc0 >> 32);
+    const uint32_t blo = (uint32_t)bdesc0, bhi = (uint32_t)(bdesc0 >> 32);
+#pragma unroll
+    for (int d = 0; d < kTcLev; d++) {
+#pragma unroll
+      for (int sa = 0; sa <= (d < kTcA - 1 ? d : kTcA - 1); sa++) {
+        const int sb = d - sa;
+        if (sb >= kTcB) continue;
+#pragma unroll
+        for (int kk = 0; kk < KR / 16; kk++) {
+          const uint64_t ad = ((uint64_t)ahi << 32) | (alo + (uint32_t)((sa * ASZ + kk * 256) >> 4));
+          const uint64_t bd = ((uint64_t)bhi << 32) | (blo + (uint32_t)((sb * BSZ + kk * 256) >> 4));
+          asm volatile("{ .reg .pred q; setp.ne.b32 q, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q; }"
+                       :: "r"(tmem + (uint32_t)(d * KR)), "l"(ad), "l"(bd), "r"(idesc), "r"((sa > 0 || kk > 0) ? 1 : 0)
+                       : "memory");
+        }
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar_a) : "memory");
+  };
+  // group exponent and digits of the tile held in xv; returns the output scale, sets flush
+  auto make_digits = [&](const double2* xv, bool& flush) {
     int em = 0;
 #pragma unroll
     for (int r = 0; r < H; r++) {
-      em = max(em, (__double2hiint(x[r].x) >> 20) & 0x7FF);
-      em = max(em, (__double2hiint(x[r].y) >> 20) & 0x7FF);
+      em = max(em, (__double2hiint(xv[r].x) >> 20) & 0x7FF);
+      em = max(em, (__double2hiint(xv[r].y) >> 20) & 0x7FF);
     }
     s_emax[part_of][row] = em;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < TPR; i++) em = max(em, s_emax[i][row]);
-    const int E = em - 1023 - 7;                  // |x| * 2^-E < 2^8
-    const float scale = E < -126 ? 0.f : __uint_as_float((uint32_t)(127 - E) << 23);
-    // digits of this thread's entries: Re -> column m0 + r, Im -> column D + m0 + r;
-    // 16-byte stores (8 columns) where the thread has them
+    // Re -> column m0 + r, Im -> column D + m0 + r; 16-byte stores (8 columns) where the thread has them
 #pragma unroll
     for (int part = 0; part < 2; part++) {
       constexpr int CW = H >= 8 ? 8 : 4;          // columns per store
 #pragma unroll
       for (int c0 = 0; c0 < H; c0 += CW) {
-        float dg[CW][kTcDig];
+        uint32_t wd[CW / 2][kTcA];
 #pragma unroll
-        for (int j = 0; j < CW; j++) {
-          const double v = part == 0 ? x[c0 + j].x : x[c0 + j].y;
-          const ArC128x::ff f = ArC128x::split((uint32_t)__double2loint(v), (uint32_t)__double2hiint(v));
-          tc_digits(f.h, f.l, scale, dg[j]);
+        for (int j = 0; j < CW; j += 2) {
+          const double va = part == 0 ? xv[c0 + j].x : xv[c0 + j].y;
+          const double vb = part == 0 ? xv[c0 + j + 1].x : xv[c0 + j + 1].y;
+          const uint32_t ha = (uint32_t)__double2hiint(va), hb = (uint32_t)__double2hiint(vb);
+          tc_digit_words(tc_window(ha, (uint32_t)__double2loint(va), em + 5),
+                         tc_window(hb, (uint32_t)__double2loint(vb), em + 5), ha, hb, wd[j / 2]);
         }
         const int col = part * D + m0 + c0;
 #pragma unroll
-        for (int s = 0; s < kTcDig; s++) {
+        for (int s = 0; s < kTcA; s++) {
           if constexpr (CW == 8)
             *reinterpret_cast<uint4*>(sA + s * ASZ + kmaj16_off(row, col, KR)) =
-                make_uint4(pack_h2(dg[0][s], dg[1][s]), pack_h2(dg[2][s], dg[3][s]),
-                           pack_h2(dg[4][s], dg[5][s]), pack_h2(dg[6][s], dg[7][s]));
+                make_uint4(wd[0][s], wd[1][s], wd[2][s], wd[3][s]);
           else
-            *reinterpret_cast<uint2*>(sA + s * ASZ + kmaj16_off(row, col, KR)) =
-                make_uint2(pack_h2(dg[0][s], dg[1][s]), pack_h2(dg[2][s], dg[3][s]));
+            *reinterpret_cast<uint2*>(sA + s * ASZ + kmaj16_off(row, col, KR)) = make_uint2(wd[0][s], wd[1][s]);
         }
       }
     }
+    // value = sum * 2^(E - 1077 + eu) (E: exponent field); groups below 2^-959 give zero
+    flush = em + eu < 64;
+    return em - 1077 + eu + sh;
+  };
+  // per tile: digits, MMAs (the next tile's loads in flight meanwhile), epilogue
+  double2 x[H];
+  uint64_t base = 0;
+  if (blockIdx.x < g.ntiles) {
+    base = tile_base(blockIdx.x);
+#pragma unroll
+    for (int r = 0; r < H; r++) x[r] = st[base + moff[r]];
+  }
+  bool ok = true;
+  for (uint64_t T = blockIdx.x; T < g.ntiles && ok; T += gridDim.x) {
+    const uint64_t cbase = base;
+    bool cflush;
+    const int cscale = make_digits(x, cflush);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (t == 0) {
-      // 21 digit-matrix products, level d = sa + sb into accumulator d
-#pragma unroll
-      for (int d = 0; d < kTcLev; d++) {
-#pragma unroll
-        for (int sa = 0; sa <= d; sa++) {
-          const int sb = d - sa;
-#pragma unroll
-          for (int kk = 0; kk < KR / 16; kk++) {
-            const uint64_t ad = umma_desc(aS + sa * ASZ + kk * 256, 128, SBO);
-            const uint64_t bd = umma_desc(bS + sb * BSZ + kk * 256, 128, SBO);
-            const uint32_t acc = (sa > 0 || kk > 0) ? 1u : 0u;
-            asm volatile("{ .reg .pred q; setp.ne.b32 q, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q; }"
-                         :: "r"(tmem + (uint32_t)(d * KR)), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
-          }
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar_a) : "memory");
-    }
-    // prefetch the next tile while the tensor cores work
-    const uint64_t curbase = base;
-    const int Ecur = E;
+    if (t == 0) issue_mma();
     const uint64_t Tn = T + gridDim.x;
     if (Tn < g.ntiles) {
       base = tile_base(Tn);
 #pragma unroll
       for (int r = 0; r < H; r++) x[r] = st[base + moff[r]];
     }
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; it++)
-      asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
-                   : "=r"(done) : "r"(mbar_a), "r"(phase) : "memory");
-    phase ^= 1u;
-    done = __syncthreads_and(done);   // one decision for the whole CTA (tcgen05.ld is warp-collective)
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!done) {
-      if (t == 0) atomicAdd(&g_tc_timeouts, 1);
-      ok = false;
-    } else {
-      const uint32_t lane = tmem + ((uint32_t)(32 * (w & 3)) << 16);
-      constexpr int NC = 4;
-#pragma unroll
-      for (int c = 0; c < H; c += NC) {
-        uint32_t re[kTcLev][NC], im[kTcLev][NC];
-#pragma unroll
-        for (int d = 0; d < kTcLev; d++) {
-          tmem_ld<NC>(lane + (uint32_t)(d * KR + m0 + c), re[d]);
-          tmem_ld<NC>(lane + (uint32_t)(d * KR + D + m0 + c), im[d]);
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < NC; j++) {
-          float Dr[kTcLev], Di[kTcLev];
-#pragma unroll
-          for (int d = 0; d < kTcLev; d++) { Dr[d] = __uint_as_float(re[d][j]); Di[d] = __uint_as_float(im[d][j]); }
-          const double vr = Ecur < -126 ? 0.0 : tc_scale(tc_combine(Dr), Ecur - 8 + eu);
-          const double vi = Ecur < -126 ? 0.0 : tc_scale(tc_combine(Di), Ecur - 8 + eu);
-          st[curbase + moff[c + j]] = make_double2(vr, vi);
-        }
-      }
-    }
+    ok = mma_wait();
+    if (ok) epilogue(cbase, cscale, cflush);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
+  // a wait gave up: its MMAs may still write tensor memory; wait once more (bounded) before freeing it
+  if (!ok) mma_wait();
   __syncthreads();
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL) : "memory");
 }
@@ -1489,11 +1544,19 @@ int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
     U.u[i] = make_double2(op.U[2 * i], op.U[2 * i + 1]);
     umax = std::max(umax, std::max(std::fabs(op.U[2 * i]), std::fabs(op.U[2 * i + 1])));
   }
-  // digits of the matrix scaled by 2^(8 - eu) with |entries| < 2^eu (eu = 1 for a unitary
-  // with an entry of modulus 1; any matrix is allowed)
+  // digits of the matrix scaled by 2^(7 - eu) with |entries| < 2^eu (any matrix is allowed)
   const int eu = umax > 0.0 ? std::ilogb(umax) + 1 : 0;
   if (eu > 100 || eu < -100) return qc_fail(QC_ERR_ARG, "matrix entries out of range for the tensor-core path");
-  const size_t smem = (size_t)kTcDig * (128 * KR * 2 + KR * KR * 2);
+  // each output of a group, in units of its lowest level, is below S 2^(55 - eu), S the largest
+  // row sum of |Re| + |Im|; the epilogue keeps it to 2^51 by dropping sh low bits
+  double S = 0.0;
+  for (int j = 0; j < D; j++) {
+    double r = 0.0;
+    for (int l = 0; l < D; l++) r += std::fabs(op.U[2 * (j * D + l)]) + std::fabs(op.U[2 * (j * D + l) + 1]);
+    S = std::max(S, r);
+  }
+  const int sh = S > 0.0 ? std::max(0, (int)std::ceil(std::log2(S * (1.0 + 0x1p-30))) + 4 - eu) : 0;
+  const size_t smem = (size_t)kTcA * 128 * KR * 2 + (size_t)kTcB * KR * KR * 2;
   static int per_sm = 0;
   if (per_sm == 0) {
     QC_CUDA(cudaFuncSetAttribute(k_fused_tc128<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1514,7 +1577,7 @@ int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
   }
   const uint64_t cap = (uint64_t)qc_num_sms() * per_sm;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
-  k_fused_tc128<K><<<grid, Tc128Cfg<K>::NT, smem, s->stream>>>((double2*)s->ptr, g, U, eu);
+  k_fused_tc128<K><<<grid, Tc128Cfg<K>::NT, smem, s->stream>>>((double2*)s->ptr, g, U, eu, sh);
   QC_LAUNCHED("k_fused_tc128");
   return QC_OK;
 }

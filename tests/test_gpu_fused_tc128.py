@@ -2,8 +2,9 @@
 
 A dense k-qubit block (k = 3..5) on a complex128 state with float-float
 arithmetic runs as one GEMM per 128-group tile on fp16 tensor cores: each
-entry is cut into six exact 9-bit digits (per-group scale for the state,
-2^-8 for the unitary) and the digit products are accumulated by level.  These
+state entry is rounded to 48 bits against its group's largest exponent and cut
+into six base-2^8 digits, each matrix entry into seven, and the digit products
+are accumulated by level in exact FP32 integer sums.  These
 cases compare it with the FP64 oracle at the complex128 tolerance (1e-12 max
 abs) and with the CUDA-core float-float path, on states whose groups mix
 large, tiny and zero amplitudes, on an unnormalised vector (amplitudes up to
