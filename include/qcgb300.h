@@ -104,9 +104,13 @@ int qc_set_stream(qc_state* s, void* cuda_stream);
 /* Select the arithmetic for complex128 gate sweeps (qc_arith). */
 int qc_set_arith(qc_state* s, int arith);
 
-/* complex64 dense blocks on k >= 3 qubits (fused gates, qc_apply_kq) run on
- * the tensor cores (tcgen05, split-TF32: hi*hi + hi*lo + lo*hi in FP32) when
- * enable != 0 (the default), else on the CUDA cores in FP32. */
+/* Dense blocks on k = 3..5 qubits (fused gates, qc_apply_kq) run on the
+ * tensor cores when enable != 0 (the default), else on the CUDA cores:
+ * complex64 with split-TF32 products (hi*hi + hi*lo + lo*hi, FP32
+ * accumulators); complex128 under QC_ARITH_F32X2 with exact fp16 digit slices
+ * (entries rounded to 48 bits against their group's largest exponent, six
+ * base-2^8 digits; the matrix in seven; exact integer level sums; error about
+ * 2^-47 of each 128-group's largest amplitude). */
 int qc_set_fused_tc(qc_state* s, int enable);
 
 /* complex128 float-float dense and phase sweeps use packed FP32-pair
