@@ -436,6 +436,7 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   const uint32_t aH = (uint32_t)__cvta_generic_to_shared(sAh), aL = (uint32_t)__cvta_generic_to_shared(sAl);
   const uint32_t bH = (uint32_t)__cvta_generic_to_shared(sBh), bL = (uint32_t)__cvta_generic_to_shared(sBl);
+  const uint64_t adH = umma_desc(aH, 128, SBO), bdH = umma_desc(bH, 128, SBO);
   const uint32_t L = 1u << g.lb;
   const uint64_t* moff = s_moff + m0;             // shared-memory table (broadcast reads)
   const uint64_t goff = g.goff[row];
@@ -480,15 +481,17 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
       // columns [0, KR): hi*hi; columns [KR, 2KR): hi*lo + lo*hi.  Keeping the
       // small products in their own accumulator stops the tensor core's FP32
       // accumulation from dropping their low bits against the large sum.
+      // Descriptors: the start address (>> 4) is the low 14 bits and every
+      // operand lies below 2^18 bytes, so an offset is one 32-bit addition.
 #pragma unroll
       for (int p = 0; p < 3; p++) {
-        const uint32_t a = p == 2 ? aL : aH;
-        const uint32_t b = p == 1 ? bL : bH;
         const uint32_t d = p == 0 ? tmem : tmem + (uint32_t)KR;
+        const uint32_t alo = (uint32_t)adH + (p == 2 ? (uint32_t)((aL - aH) >> 4) : 0u);
+        const uint32_t blo = (uint32_t)bdH + (p == 1 ? (uint32_t)((bL - bH) >> 4) : 0u);
 #pragma unroll
         for (int kk = 0; kk < KR / 8; kk++) {
-          const uint64_t ad = umma_desc(a + kk * 256, 128, SBO);
-          const uint64_t bd = umma_desc(b + kk * 256, 128, SBO);
+          const uint64_t ad = (adH & 0xFFFFFFFF00000000ull) | (alo + (uint32_t)(kk * 16));
+          const uint64_t bd = (bdH & 0xFFFFFFFF00000000ull) | (blo + (uint32_t)(kk * 16));
           const uint32_t acc = (p == 2 || kk > 0) ? 1u : 0u;
           asm volatile("{ .reg .pred q; setp.ne.b32 q, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q; }"
                        :: "r"(d), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
@@ -627,7 +630,8 @@ __device__ __forceinline__ uint32_t tc_int22(float x) { return (uint32_t)__float
 // remainder (-1, 0 or 1, exact) moves into the next level's float.  The total
 // is a 64-bit integer; shifted right by sh (|total| <= 2^(51 + sh), chosen by
 // the host from the matrix) it sits in the mantissa of 1.5 * 2^52 + total,
-// so one double subtraction converts it exactly.
+// so one double subtraction converts it exactly (an integer-only conversion
+// measured slower: the FP64 pipe is otherwise idle here, the integer pipe is not).
 template <bool SMALL>
 __device__ __forceinline__ double tc_assemble(const float* D, int sh, long long rnd, int scale, bool flush) {
   constexpr uint32_t C1 = 0x4B400000u;            // bits of 1.5 * 2^23
