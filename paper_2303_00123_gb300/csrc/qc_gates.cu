@@ -724,8 +724,6 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  // kind::f16: D = F32 (bit 4), A = B = F16 (formats 0), both K-major, N = KR, M = 128
-  const uint32_t idesc = (1u << 4) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   const uint32_t aS = (uint32_t)__cvta_generic_to_shared(sA), bS = (uint32_t)__cvta_generic_to_shared(sB);
   const long long rnd = sh > 0 ? 1ll << (sh - 1) : 0ll;   // rounds the total to a multiple of 2^sh
   const uint32_t L = 1u << g.lb;
@@ -772,30 +770,42 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
       }
     }
   };
-  // 27 digit-matrix products, level d = sa + sb into accumulator d.  Descriptors:
-  // the start address (>> 4) is the low 14 bits and every operand lies below
-  // 2^18 bytes, so an offset is one 32-bit addition to the low word.
+  // The 27 digit-matrix products (level d = sa + sb into accumulator d) as few,
+  // wide MMAs: the matrix digits are stored back to back, i.e. as one K-major
+  // matrix of 7 KR rows, so state digit sa against matrix digits t0 .. t0+nt-1 is
+  // one MMA with N = nt KR whose accumulator columns start at level sa + t0
+  // (N <= 256: k = 5 takes 9 MMAs per K step, k = 4 and 3 take 6).  Run by all of
+  // warp 0, the MMAs predicated on one elected lane.  Descriptors: the start
+  // address (>> 4) is the low 14 bits and every operand lies below 2^18 bytes, so
+  // an offset is one 32-bit addition to the low word.
   auto issue_mma = [&]() {
+    uint32_t lead;
+    asm volatile("{ .reg .pred p; elect.sync _|p, 0xffffffff; selp.u32 %0, 1, 0, p; }" : "=r"(lead));
     const uint64_t adesc0 = umma_desc(aS, 128, SBO), bdesc0 = umma_desc(bS, 128, SBO);
     const uint32_t alo = (uint32_t)adesc0, ahi = (uint32_t)(adesc0 >> 32);
     const uint32_t blo = (uint32_t)bdesc0, bhi = (uint32_t)(bdesc0 >> 32);
+    constexpr int TMAX = 256 / KR;                // matrix digits per MMA
 #pragma unroll
-    for (int d = 0; d < kTcLev; d++) {
+    for (int sa = 0; sa < kTcA; sa++) {
 #pragma unroll
-      for (int sa = 0; sa <= (d < kTcA - 1 ? d : kTcA - 1); sa++) {
-        const int sb = d - sa;
-        if (sb >= kTcB) continue;
+      for (int t0 = 0; t0 < kTcLev - sa; t0 += TMAX) {
+        const int nt = (kTcLev - sa - t0) < TMAX ? (kTcLev - sa - t0) : TMAX;
+        // kind::f16: D = F32 (bit 4), A = B = F16 (formats 0), both K-major, N = nt KR, M = 128
+        const uint32_t idn = (1u << 4) | ((uint32_t)((nt * KR) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 #pragma unroll
         for (int kk = 0; kk < KR / 16; kk++) {
           const uint64_t ad = ((uint64_t)ahi << 32) | (alo + (uint32_t)((sa * ASZ + kk * 256) >> 4));
-          const uint64_t bd = ((uint64_t)bhi << 32) | (blo + (uint32_t)((sb * BSZ + kk * 256) >> 4));
-          asm volatile("{ .reg .pred q; setp.ne.b32 q, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q; }"
-                       :: "r"(tmem + (uint32_t)(d * KR)), "l"(ad), "l"(bd), "r"(idesc), "r"((sa > 0 || kk > 0) ? 1 : 0)
-                       : "memory");
+          const uint64_t bd = ((uint64_t)bhi << 32) | (blo + (uint32_t)((t0 * BSZ + kk * 256) >> 4));
+          asm volatile("{ .reg .pred q, e; setp.ne.b32 q, %4, 0; setp.ne.b32 e, %5, 0;\n"
+                       "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q; }"
+                       :: "r"(tmem + (uint32_t)((sa + t0) * KR)), "l"(ad), "l"(bd), "r"(idn),
+                          "r"((sa > 0 || kk > 0) ? 1 : 0), "r"(lead) : "memory");
         }
       }
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar_a) : "memory");
+    asm volatile("{ .reg .pred e; setp.ne.b32 e, %1, 0;\n"
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0]; }"
+                 :: "r"(mbar_a), "r"(lead) : "memory");
   };
   // group exponent and digits of the tile held in xv; returns the output scale, sets flush
   auto make_digits = [&](const double2* xv, bool& flush) {
@@ -856,7 +866,7 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (t == 0) issue_mma();
+    if (w == 0) issue_mma();
     const uint64_t Tn = T + gridDim.x;
     if (Tn < g.ntiles) {
       base = tile_base(Tn);
