@@ -434,6 +434,7 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  const uint32_t idesc2 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)((2 * KR) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   const uint32_t aH = (uint32_t)__cvta_generic_to_shared(sAh), aL = (uint32_t)__cvta_generic_to_shared(sAl);
   const uint32_t bH = (uint32_t)__cvta_generic_to_shared(sBh), bL = (uint32_t)__cvta_generic_to_shared(sBl);
   const uint64_t adH = umma_desc(aH, 128, SBO), bdH = umma_desc(bH, 128, SBO);
@@ -483,18 +484,21 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
       // accumulation from dropping their low bits against the large sum.
       // Descriptors: the start address (>> 4) is the low 14 bits and every
       // operand lies below 2^18 bytes, so an offset is one 32-bit addition.
+      // Bh and Bl are stored back to back: Ah against both is one MMA of N = 2 KR
+      // (hi*hi into columns [0, KR), hi*lo into [KR, 2KR)), then Al*Bh into [KR, 2KR).
 #pragma unroll
-      for (int p = 0; p < 3; p++) {
+      for (int p = 0; p < 2; p++) {
         const uint32_t d = p == 0 ? tmem : tmem + (uint32_t)KR;
-        const uint32_t alo = (uint32_t)adH + (p == 2 ? (uint32_t)((aL - aH) >> 4) : 0u);
-        const uint32_t blo = (uint32_t)bdH + (p == 1 ? (uint32_t)((bL - bH) >> 4) : 0u);
+        const uint32_t alo = (uint32_t)adH + (p == 1 ? (uint32_t)((aL - aH) >> 4) : 0u);
+        const uint32_t blo = (uint32_t)bdH;
+        const uint32_t id = p == 0 ? idesc2 : idesc;
 #pragma unroll
         for (int kk = 0; kk < KR / 8; kk++) {
           const uint64_t ad = (adH & 0xFFFFFFFF00000000ull) | (alo + (uint32_t)(kk * 16));
           const uint64_t bd = (bdH & 0xFFFFFFFF00000000ull) | (blo + (uint32_t)(kk * 16));
-          const uint32_t acc = (p == 2 || kk > 0) ? 1u : 0u;
+          const uint32_t acc = (p == 1 || kk > 0) ? 1u : 0u;
           asm volatile("{ .reg .pred q; setp.ne.b32 q, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q; }"
-                       :: "r"(d), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                       :: "r"(d), "l"(ad), "l"(bd), "r"(id), "r"(acc) : "memory");
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar_a) : "memory");
