@@ -136,6 +136,30 @@ def test_fusion_of_brickwork_reduces_sweeps(q):
     assert counts[5] < counts[4] < counts[3] < counts[2] < counts[0]
 
 
+@pytest.mark.parametrize("fuse_k", [3, 4, 5])
+def test_partial_block_emission_reproduces_the_circuit(q, fuse_k):
+    """When a gate would widen a block past k qubits the planner emits only the
+    fullest touched blocks and keeps growing the rest: deep brickwork, Trotter
+    and random circuits exercise that path; the oracle applies plan and gates."""
+    from oracle import oracle as O
+    from paper_2303_00123_gb300 import circuits as C
+    n = 10
+    for gates in (C.brickwork(n, 12, seed=31), C.tfxy_trotter(n, 3, seed=32), C.random_mix(n, 200, seed=33)):
+        plan = q.fuse_plan(n, gates, fuse_k)
+        phi = C.random_state(n, 34)
+        psi = phi.copy()
+        apply_plan(O, psi, n, plan)
+        np.testing.assert_allclose(psi, O.run_circuit(n, gates, phi), atol=1e-12)
+
+
+def test_fusion_block_counts_at_n30(q):
+    """Sweeps the planner makes for the n=30 workloads (each block is one pass over
+    the state): brickwork depth 40 and TFXY 10 steps at k=5."""
+    from paper_2303_00123_gb300 import circuits as C
+    assert len(q.fuse_plan(30, C.brickwork(30, 40, seed=2001), 5)) <= 150
+    assert len(q.fuse_plan(30, C.tfxy_trotter(30, 10, seed=1003), 5)) <= 80
+
+
 def test_count_params(q):
     from paper_2303_00123_gb300 import circuits as C
     n, layers = 5, 3
