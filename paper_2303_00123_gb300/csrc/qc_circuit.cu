@@ -167,7 +167,7 @@ struct Emitted {
 
 // Greedy fusion with several open blocks on disjoint qubit sets: a gate joins
 // (and merges) the open blocks it touches when the union has at most kmax
-// qubits; otherwise those blocks are emitted and the gate opens a new block.
+// qubits; otherwise touched blocks are emitted, largest first, until it fits.
 // Blocks on disjoint qubits commute, so emission order stays valid.
 void fuse(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Emitted>& out) {
   std::vector<Block> open;
@@ -250,6 +250,96 @@ void fuse(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Emitt
   for (int i : rest) emit(i);
 }
 
+// Fusion from the dependency front, one block at a time: a gate is ready when
+// every earlier gate on its qubits has been taken.  A block starts at the
+// earliest remaining gate (always ready), takes every ready gate inside its
+// qubit set, and widens by the qubits of the earliest ready gate that keeps it
+// within kmax, until neither is possible.  Gates taken in this order respect
+// every qubit's gate order, so the emitted sequence equals the circuit.
+void fuse_front(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Emitted>& out) {
+  const int G = (int)gates.size();
+  std::vector<std::vector<int>> on_q(n), qs_of(G);
+  for (int i = 0; i < G; i++) {
+    const Resolved& R = gates[i];
+    qs_of[i].assign(R.t, R.t + R.k);
+    qs_of[i].insert(qs_of[i].end(), R.c, R.c + R.nc);
+    for (int q : qs_of[i]) on_q[q].push_back(i);
+  }
+  std::vector<int> pos(n, 0);
+  std::vector<char> taken(G, 0);
+  auto ready = [&](int i) {
+    if (taken[i]) return false;
+    for (int q : qs_of[i]) if (on_q[q][pos[q]] != i) return false;
+    return true;
+  };
+  auto take = [&](int i) {
+    taken[i] = 1;
+    for (int q : qs_of[i]) pos[q]++;
+  };
+  int next = 0;
+  while (true) {
+    while (next < G && taken[next]) next++;
+    if (next >= G) break;
+    const int seed = next;                       // all its predecessors are taken
+    if ((int)qs_of[seed].size() > kmax) {
+      take(seed);
+      Emitted e;
+      e.single = true;
+      e.gate = seed;
+      out.push_back(std::move(e));
+      continue;
+    }
+    Block b;
+    b.ngates = 0;
+    for (int q : qs_of[seed]) {
+      Block id = single_qubit_identity(q);
+      if (b.q.empty()) { b.q = id.q; b.M = id.M; }
+      else kron_into(b, id);
+    }
+    b.first = seed;
+    for (bool grown = true; grown;) {
+      // every ready gate inside the block's qubits
+      for (bool more = true; more;) {
+        more = false;
+        for (size_t j = 0; j < b.q.size(); j++) {
+          const int q = b.q[j];
+          while (pos[q] < (int)on_q[q].size()) {
+            const int i = on_q[q][pos[q]];
+            bool inside = ready(i);
+            for (int qq : qs_of[i]) if (inside && local_index(b, qq) < 0) inside = false;
+            if (!inside) break;
+            block_apply(b, gates[i]);
+            take(i);
+            more = true;
+          }
+        }
+      }
+      // widen by the earliest ready gate on the block's qubits that fits
+      grown = false;
+      int best = -1;
+      for (size_t j = 0; j < b.q.size(); j++) {
+        const int q = b.q[j];
+        if (pos[q] >= (int)on_q[q].size()) continue;
+        const int i = on_q[q][pos[q]];
+        if (!ready(i)) continue;
+        int width = (int)b.q.size();
+        for (int qq : qs_of[i]) if (local_index(b, qq) < 0) width++;
+        if (width <= kmax && (best < 0 || i < best)) best = i;
+      }
+      if (best >= 0) {
+        for (int qq : qs_of[best])
+          if (local_index(b, qq) < 0) kron_into(b, single_qubit_identity(qq));
+        grown = true;
+      }
+    }
+    Emitted e;
+    e.single = (b.ngates == 1);
+    e.gate = seed;
+    if (!e.single) e.block = std::move(b);
+    out.push_back(std::move(e));
+  }
+}
+
 }  // namespace
 
 int qc_gate_to_op(int n, const qc_gate& g, qc_op& op) {
@@ -298,8 +388,11 @@ void emit_matrix_segment(int n, const std::vector<Resolved>& res, int begin, int
                          std::vector<qc_op>& ops) {
   if (begin >= end) return;
   std::vector<Resolved> seg(res.begin() + begin, res.begin() + end);
-  std::vector<Emitted> em;
+  // two planners; the plan with fewer sweeps is kept (ties: the first)
+  std::vector<Emitted> em, em2;
   fuse(n, seg, std::min(fuse_k, n), em);
+  fuse_front(n, seg, std::min(fuse_k, n), em2);
+  if (em2.size() < em.size()) em.swap(em2);
   for (size_t i = 0; i < em.size(); i++) {
     qc_op op;
     if (em[i].single) { to_op(n, seg[em[i].gate], op); ops.push_back(op); continue; }
