@@ -340,6 +340,82 @@ void fuse_front(int n, const std::vector<Resolved>& gates, int kmax, std::vector
   }
 }
 
+// Merge pass over a plan: an entry moves back past earlier entries on other
+// qubits (they commute) and joins the first earlier entry whose qubits it
+// shares or with which it fits in kmax qubits -- it joins when the union fits,
+// and stops where it does not.  Repeated until nothing merges.  A merged entry
+// is a dense block (left product in FP64); unmerged single gates stay as they
+// are, so structured kernels (permutations, phases) keep serving them.
+void merge_pass(const std::vector<Resolved>& gates, int kmax, std::vector<Emitted>& em) {
+  auto qubits_of = [&](const Emitted& e) {
+    std::vector<int> qs;
+    if (e.single) {
+      const Resolved& R = gates[e.gate];
+      qs.assign(R.t, R.t + R.k);
+      qs.insert(qs.end(), R.c, R.c + R.nc);
+    } else {
+      qs = e.block.q;
+    }
+    return qs;
+  };
+  auto as_block = [&](const Emitted& e) {
+    if (!e.single) return e.block;
+    const Resolved& R = gates[e.gate];
+    Block b;
+    std::vector<int> qs(R.t, R.t + R.k);
+    qs.insert(qs.end(), R.c, R.c + R.nc);
+    for (int q : qs) {
+      Block id = single_qubit_identity(q);
+      if (b.q.empty()) { b.q = id.q; b.M = id.M; }
+      else kron_into(b, id);
+    }
+    block_apply(b, R);
+    b.first = e.gate;
+    return b;
+  };
+  for (bool changed = true; changed;) {
+    changed = false;
+    std::vector<Emitted> out;
+    std::vector<std::vector<int>> oq;   // qubits of each out entry
+    for (Emitted& e : em) {
+      const std::vector<int> qe = qubits_of(e);
+      int target = -1;
+      for (int i = (int)out.size() - 1; i >= 0; i--) {
+        int uni = (int)oq[i].size(), shared = 0;
+        for (int q : qe) {
+          if (std::find(oq[i].begin(), oq[i].end(), q) != oq[i].end()) shared++;
+          else uni++;
+        }
+        if ((int)qe.size() <= kmax && uni <= kmax) { target = i; break; }
+        if (shared) break;
+      }
+      if (target < 0) {
+        oq.push_back(qe);
+        out.push_back(std::move(e));
+        continue;
+      }
+      // out[target] then e, as one block on the union of their qubits
+      Block b = as_block(out[target]);
+      const Block be = as_block(e);
+      for (int q : be.q)
+        if (local_index(b, q) < 0) kron_into(b, single_qubit_identity(q));
+      Resolved R;
+      R.k = (int)be.q.size();
+      R.nc = 0;
+      for (int j = 0; j < R.k; j++) R.t[j] = be.q[j];
+      R.U = be.M;
+      const int ng = b.ngates + be.ngates;
+      block_apply(b, R);
+      b.ngates = ng;
+      out[target].single = false;
+      out[target].block = std::move(b);
+      oq[target] = out[target].block.q;
+      changed = true;
+    }
+    em.swap(out);
+  }
+}
+
 }  // namespace
 
 int qc_gate_to_op(int n, const qc_gate& g, qc_op& op) {
@@ -393,6 +469,7 @@ void emit_matrix_segment(int n, const std::vector<Resolved>& res, int begin, int
   fuse(n, seg, std::min(fuse_k, n), em);
   fuse_front(n, seg, std::min(fuse_k, n), em2);
   if (em2.size() < em.size()) em.swap(em2);
+  merge_pass(seg, std::min(fuse_k, n), em);
   for (size_t i = 0; i < em.size(); i++) {
     qc_op op;
     if (em[i].single) { to_op(n, seg[em[i].gate], op); ops.push_back(op); continue; }
