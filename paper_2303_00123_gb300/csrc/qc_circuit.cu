@@ -464,12 +464,14 @@ void emit_matrix_segment(int n, const std::vector<Resolved>& res, int begin, int
                          std::vector<qc_op>& ops) {
   if (begin >= end) return;
   std::vector<Resolved> seg(res.begin() + begin, res.begin() + end);
-  // two planners; the plan with fewer sweeps is kept (ties: the first)
+  // two planners, each followed by the merge pass; the plan with fewer sweeps
+  // is kept (ties: the first)
   std::vector<Emitted> em, em2;
   fuse(n, seg, std::min(fuse_k, n), em);
-  fuse_front(n, seg, std::min(fuse_k, n), em2);
-  if (em2.size() < em.size()) em.swap(em2);
   merge_pass(seg, std::min(fuse_k, n), em);
+  fuse_front(n, seg, std::min(fuse_k, n), em2);
+  merge_pass(seg, std::min(fuse_k, n), em2);
+  if (em2.size() < em.size()) em.swap(em2);
   for (size_t i = 0; i < em.size(); i++) {
     qc_op op;
     if (em[i].single) { to_op(n, seg[em[i].gate], op); ops.push_back(op); continue; }
