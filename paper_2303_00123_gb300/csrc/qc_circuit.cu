@@ -340,12 +340,13 @@ void fuse_front(int n, const std::vector<Resolved>& gates, int kmax, std::vector
   }
 }
 
-// Merge pass over a plan: an entry moves back past earlier entries on other
-// qubits (they commute) and joins the first earlier entry whose qubits it
-// shares or with which it fits in kmax qubits -- it joins when the union fits,
-// and stops where it does not.  Repeated until nothing merges.  A merged entry
-// is a dense block (left product in FP64); unmerged single gates stay as they
-// are, so structured kernels (permutations, phases) keep serving them.
+// Merge pass over a plan: each entry moves back past earlier entries on
+// disjoint qubits (they commute with it) and joins the nearest earlier entry
+// whose union with it has at most kmax qubits; it stays where it is when it
+// reaches an entry it shares a qubit with and their union is wider.  Repeated
+// until nothing merges.  A merged entry is a dense block (left product in
+// FP64); unmerged single gates stay as they are, so structured kernels
+// (permutations, phases) keep serving them.
 void merge_pass(const std::vector<Resolved>& gates, int kmax, std::vector<Emitted>& em) {
   auto qubits_of = [&](const Emitted& e) {
     std::vector<int> qs;
