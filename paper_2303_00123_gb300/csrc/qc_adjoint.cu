@@ -61,6 +61,28 @@ __device__ __forceinline__ double block_sum_d(double v) {
   return t;
 }
 
+// Block sum in the state's precision class: complex64 states reduce in FP32
+// within a block (256 products of FP32 values; GB300's FP64 pipe runs at a
+// small fraction of the FP32 rate), complex128 in FP64; block totals are
+// summed across blocks in FP64.
+__device__ __forceinline__ float block_sum_f(float v) {
+  __shared__ float redf[kT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) redf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < kT / 32 ? redf[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  __syncthreads();
+  return t;
+}
+__device__ __forceinline__ double block_sum_r(float v) { return (double)block_sum_f(v); }
+__device__ __forceinline__ double block_sum_r(double v) { return block_sum_d(v); }
+
 // ---------------------------------------------------------------- gates
 struct BGeom {
   uint64_t ngroups;       // groups per state
@@ -111,7 +133,7 @@ k_adj_param(typename Ar::raw_t* __restrict__ work, uint64_t nstate, int B, int t
   typename Ar::raw_t* phi = work + (size_t)s * nstate;
   typename Ar::raw_t* lam = work + (size_t)(B + s) * nstate;
   const uint64_t npairs = nstate >> 1, off = 1ull << t;
-  double acc = 0.0;
+  R acc = 0;
   for (uint64_t j = (uint64_t)blockIdx.x * kT + threadIdx.x; j < npairs; j += (uint64_t)gridDim.x * kT) {
     const uint64_t a = qc_insert_zero(j, t), b = a + off;
     const typename Ar::raw_t pa = phi[a], pb = phi[b], la = lam[a], lb = lam[b];
@@ -125,7 +147,7 @@ k_adj_param(typename Ar::raw_t* __restrict__ work, uint64_t nstate, int B, int t
     } else {             // Y: -Re(conj(la) pb) + Re(conj(lb) pa)
       c = -(lar * pbr + lai * pbi) + (lbr * par + lbi * pai);
     }
-    acc += (double)c;
+    acc += c;
     typename Ar::val_t v[2];
     v[0] = Ar::from_raw(pa); v[1] = Ar::from_raw(pb);
     phi[a] = Ar::to_raw(Ar::template dot<2>(&M[0], v));
@@ -134,7 +156,7 @@ k_adj_param(typename Ar::raw_t* __restrict__ work, uint64_t nstate, int B, int t
     lam[a] = Ar::to_raw(Ar::template dot<2>(&M[0], v));
     lam[b] = Ar::to_raw(Ar::template dot<2>(&M[2], v));
   }
-  const double tot = block_sum_d(acc);
+  const double tot = block_sum_r(acc);
   if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = tot;
 }
 
@@ -174,12 +196,13 @@ k_energy(const T* __restrict__ work, uint64_t nstate, int B, double* __restrict_
   const int s = blockIdx.y;
   const T* phi = work + (size_t)s * nstate;
   const T* lam = work + (size_t)(B + s) * nstate;
-  double acc = 0.0;
+  using R = decltype(T::x);
+  R acc = 0;
   for (uint64_t z = (uint64_t)blockIdx.x * kT + threadIdx.x; z < nstate; z += (uint64_t)gridDim.x * kT) {
     const T a = phi[z], b = lam[z];
-    acc += (double)(a.x * b.x + a.y * b.y);
+    acc += a.x * b.x + a.y * b.y;
   }
-  const double tot = block_sum_d(acc);
+  const double tot = block_sum_r(acc);
   if (threadIdx.x == 0) partial[(size_t)s * gridDim.x + blockIdx.x] = tot;
 }
 
