@@ -152,6 +152,59 @@ def test_partial_block_emission_reproduces_the_circuit(q, fuse_k):
         np.testing.assert_allclose(psi, O.run_circuit(n, gates, phi), atol=1e-12)
 
 
+def _mixed_circuit(n, ngates, seed):
+    """Random gates of every kind the planner treats differently: dense 1q and
+    2q, (doubly) controlled gates with control states 0/1, runs of disjoint SWAPs,
+    runs of controlled phases sharing a qubit, named gates."""
+    from paper_2303_00123_gb300 import circuits as C
+    from paper_2303_00123_gb300.circuits import Gate
+    rng = np.random.default_rng(seed)
+    g = []
+    while len(g) < ngates:
+        r = rng.random()
+        qs = [int(v) for v in rng.choice(n, size=min(n, 4), replace=False)]
+        if r < 0.3:
+            g.append(Gate("U", (qs[0],), matrix=C.haar_unitary(rng, 2)))
+        elif r < 0.45:
+            g.append(Gate("U4", (qs[0], qs[1]), matrix=C.haar_unitary(rng, 4)))
+        elif r < 0.6:
+            g.append(Gate("X", (qs[0],), controls=(qs[1],), cstates=(int(rng.integers(2)),)))
+        elif r < 0.7 and n >= 3:
+            g.append(Gate("U", (qs[0],), controls=(qs[1], qs[2]), cstates=(int(rng.integers(2)), 1),
+                          matrix=C.haar_unitary(rng, 2)))
+        elif r < 0.8 and n >= 4:
+            g.append(Gate("SWAP", (qs[0], qs[1])))
+            g.append(Gate("SWAP", (qs[2], qs[3])))
+        elif r < 0.9:
+            for other in qs[1:]:
+                g.append(Gate("P", (qs[0],), controls=(other,), theta=float(rng.uniform(-3, 3))))
+        else:
+            g.append(Gate(["H", "S", "T", "RX", "RY", "RZ"][int(rng.integers(6))], (qs[0],),
+                          theta=float(rng.uniform(-3, 3))))
+    return g
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_fusion_plans_of_random_mixed_circuits(q, seed):
+    """Property: for random mixed circuits (n = 4..7) and every fusion width,
+    the planned entries applied with the oracle equal the circuit applied gate
+    by gate, and no dense block exceeds the width."""
+    from oracle import oracle as O
+    from paper_2303_00123_gb300 import circuits as C
+    n = 4 + seed % 4
+    gates = _mixed_circuit(n, 60, 500 + seed)
+    phi = C.random_state(n, 600 + seed)
+    ref = O.run_circuit(n, gates, phi)
+    for k in (2, 3, 4, 5):
+        plan = q.fuse_plan(n, gates, k)
+        for b in plan:
+            if b[0] not in ("phase", "swap") and len(b[0]) + len(b[1]) > max(k, 3):
+                raise AssertionError("block wider than k=%d: %r" % (k, (b[0], b[1])))
+        psi = phi.copy()
+        apply_plan(O, psi, n, plan)
+        np.testing.assert_allclose(psi, ref, atol=1e-12, err_msg="k=%d" % k)
+
+
 def test_fusion_block_counts_at_n30(q):
     """Sweeps the planner makes for the n=30 workloads (each block is one pass over
     the state): brickwork depth 40 and TFXY 10 steps at k=5."""
