@@ -99,33 +99,10 @@ int local_index(const Block& b, int qubit) {
   return -1;
 }
 
-// Tensor product: b <- b (x) o (b's qubits stay the most significant).
-void kron_into(Block& b, const Block& o) {
-  const int ma = (int)b.q.size(), mb = (int)o.q.size();
-  const int da = 1 << ma, db = 1 << mb, d = da * db;
-  std::vector<cd> M((size_t)d * d);
-  for (int ra = 0; ra < da; ra++)
-    for (int ca = 0; ca < da; ca++) {
-      const cd x = b.M[(size_t)ra * da + ca];
-      if (x == cd(0)) continue;
-      for (int rb = 0; rb < db; rb++)
-        for (int cb = 0; cb < db; cb++)
-          M[(size_t)(ra * db + rb) * d + (ca * db + cb)] = x * o.M[(size_t)rb * db + cb];
-    }
-  b.q.insert(b.q.end(), o.q.begin(), o.q.end());
-  b.M.swap(M);
-  b.ngates += o.ngates;
-  if (o.first >= 0 && (b.first < 0 || o.first < b.first)) b.first = o.first;
-}
-
-Block single_qubit_identity(int qubit) {
-  Block b;
-  b.q = {qubit};
-  b.M = {1, 0, 0, 1};
-  return b;
-}
-
-// Apply a resolved gate to the block's matrix (left-multiply).
+// Apply a resolved gate to the block's matrix (left-multiply): for every row
+// group the gate connects (target bits of the row index running, control bits
+// at their states) the group's rows are replaced by U times them, whole rows at
+// a time.
 void block_apply(Block& b, const Resolved& R) {
   const int m = (int)b.q.size();
   const int d = 1 << m;
@@ -133,60 +110,67 @@ void block_apply(Block& b, const Resolved& R) {
   for (int i = 0; i < R.k; i++) tl[i] = m - 1 - local_index(b, R.t[i]);   // bit positions in block index
   for (int i = 0; i < R.nc; i++) cl[i] = m - 1 - local_index(b, R.c[i]);
   const int kd = 1 << R.k;
-  std::vector<cd> in(kd);
-  for (int col = 0; col < d; col++) {
-    for (int x = 0; x < d; x++) {
-      bool first = true;
-      for (int i = 0; i < R.k; i++) if ((x >> tl[i]) & 1) first = false;
-      if (!first) continue;
-      bool ok = true;
-      for (int i = 0; i < R.nc; i++) if (((x >> cl[i]) & 1) != R.cs[i]) ok = false;
-      if (!ok) continue;
-      int idx[1 << QC_MAX_TARGETS];
-      for (int r = 0; r < kd; r++) {
-        int y = x;
-        for (int i = 0; i < R.k; i++) if ((r >> (R.k - 1 - i)) & 1) y |= 1 << tl[i];
-        idx[r] = y;
-        in[r] = b.M[(size_t)y * d + col];
-      }
-      for (int r = 0; r < kd; r++) {
-        cd acc = 0;
-        for (int c = 0; c < kd; c++) acc += R.U[(size_t)r * kd + c] * in[c];
-        b.M[(size_t)idx[r] * d + col] = acc;
+  std::vector<cd> rows((size_t)kd * d);
+  for (int x = 0; x < d; x++) {
+    bool base = true;
+    for (int i = 0; i < R.k; i++) if ((x >> tl[i]) & 1) base = false;
+    for (int i = 0; i < R.nc; i++) if (((x >> cl[i]) & 1) != R.cs[i]) base = false;
+    if (!base) continue;
+    int idx[1 << QC_MAX_TARGETS];
+    for (int r = 0; r < kd; r++) {
+      int y = x;
+      for (int i = 0; i < R.k; i++) if ((r >> (R.k - 1 - i)) & 1) y |= 1 << tl[i];
+      idx[r] = y;
+      std::copy(b.M.begin() + (size_t)y * d, b.M.begin() + (size_t)(y + 1) * d, rows.begin() + (size_t)r * d);
+    }
+    for (int r = 0; r < kd; r++) {
+      cd* out = &b.M[(size_t)idx[r] * d];
+      std::fill(out, out + d, cd(0));
+      for (int c = 0; c < kd; c++) {
+        const cd u = R.U[(size_t)r * kd + c];
+        if (u == cd(0)) continue;
+        const cd* in = &rows[(size_t)c * d];
+        for (int j = 0; j < d; j++) out[j] += u * in[j];
       }
     }
   }
   b.ngates++;
 }
 
-struct Emitted {
-  bool single;      // apply the original gate
-  int gate;         // its index
-  Block block;
+
+// A planned entry: a block's qubits (q[0] = most significant bit of its
+// matrix) and its gates in application order.  One gate: applied as it is
+// (its structured kernel); more: one dense block, built once the plan is
+// chosen.  The planners below work on qubit sets and gate lists only.
+struct Planned {
+  std::vector<int> q;
+  std::vector<int> gates;
+  int first = -1;         // smallest gate index (flush order)
 };
+
+std::vector<int> gate_qubits(const Resolved& R) {
+  std::vector<int> qs(R.t, R.t + R.k);
+  qs.insert(qs.end(), R.c, R.c + R.nc);
+  return qs;
+}
+
+bool has_qubit(const std::vector<int>& qs, int q) { return std::find(qs.begin(), qs.end(), q) != qs.end(); }
 
 // Greedy fusion with several open blocks on disjoint qubit sets: a gate joins
 // (and merges) the open blocks it touches when the union has at most kmax
 // qubits; otherwise touched blocks are emitted, largest first, until it fits.
 // Blocks on disjoint qubits commute, so emission order stays valid.
-void fuse(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Emitted>& out) {
-  std::vector<Block> open;
+void fuse(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Planned>& out) {
+  std::vector<Planned> open;
   std::vector<int> owner(n, -1);   // qubit -> open block index
   auto emit = [&](int bi) {
-    Block& b = open[bi];
-    Emitted e;
-    e.single = (b.ngates == 1);
-    e.gate = b.first;
-    if (!e.single) e.block = b;
-    out.push_back(std::move(e));
+    Planned& b = open[bi];
     for (int q : b.q) owner[q] = -1;
-    b.q.clear();
-    b.ngates = 0;
+    out.push_back(std::move(b));
+    b = Planned();
   };
   for (int gi = 0; gi < (int)gates.size(); gi++) {
-    const Resolved& R = gates[gi];
-    std::vector<int> qs(R.t, R.t + R.k);
-    qs.insert(qs.end(), R.c, R.c + R.nc);
+    const std::vector<int> qs = gate_qubits(gates[gi]);
     std::vector<int> touched;
     int width = 0;
     for (int q : qs) {
@@ -197,9 +181,10 @@ void fuse(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Emitt
     for (int o : touched) width += (int)open[o].q.size();
     if ((int)qs.size() > kmax) {          // wider than a block: applied on its own
       for (int o : touched) emit(o);
-      Emitted e;
-      e.single = true;
-      e.gate = gi;
+      Planned e;
+      e.q = qs;
+      e.gates = {gi};
+      e.first = gi;
       out.push_back(std::move(e));
       continue;
     }
@@ -214,28 +199,22 @@ void fuse(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Emitt
       while (width > kmax && !touched.empty()) {
         const int o = touched.front();
         width -= (int)open[o].q.size();
-        for (int q : qs) if (local_index(open[o], q) >= 0) width++;   // its qubits in the gate become free
+        for (int q : qs) if (has_qubit(open[o].q, q)) width++;   // its qubits in the gate become free
         emit(o);
         touched.erase(touched.begin());
       }
     }
-    // merge the touched blocks (if any) into one
-    Block nb;
-    if (touched.empty()) {
-      nb.ngates = 0;
-    } else {
-      std::sort(touched.begin(), touched.end());
-      nb = open[touched[0]];
-      for (size_t i = 1; i < touched.size(); i++) kron_into(nb, open[touched[i]]);
-      for (int o : touched) { for (int q : open[o].q) owner[q] = -1; open[o].q.clear(); open[o].ngates = 0; }
+    // merge the touched blocks (if any) into one; their gates commute (disjoint qubits)
+    Planned nb;
+    std::sort(touched.begin(), touched.end());
+    for (int o : touched) {
+      for (int q : open[o].q) { nb.q.push_back(q); owner[q] = -1; }
+      nb.gates.insert(nb.gates.end(), open[o].gates.begin(), open[o].gates.end());
+      if (nb.first < 0 || open[o].first < nb.first) nb.first = open[o].first;
+      open[o] = Planned();
     }
-    for (int q : qs)
-      if (local_index(nb, q) < 0) {
-        Block id = single_qubit_identity(q);
-        if (nb.q.empty()) { nb.q = id.q; nb.M = id.M; }
-        else kron_into(nb, id);
-      }
-    block_apply(nb, R);
+    for (int q : qs) if (!has_qubit(nb.q, q)) nb.q.push_back(q);
+    nb.gates.push_back(gi);
     if (nb.first < 0) nb.first = gi;
     int slot = -1;
     for (int i = 0; i < (int)open.size(); i++) if (open[i].q.empty()) { slot = i; break; }
@@ -256,13 +235,11 @@ void fuse(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Emitt
 // qubit set, and widens by the qubits of the earliest ready gate that keeps it
 // within kmax, until neither is possible.  Gates taken in this order respect
 // every qubit's gate order, so the emitted sequence equals the circuit.
-void fuse_front(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Emitted>& out) {
+void fuse_front(int n, const std::vector<Resolved>& gates, int kmax, std::vector<Planned>& out) {
   const int G = (int)gates.size();
   std::vector<std::vector<int>> on_q(n), qs_of(G);
   for (int i = 0; i < G; i++) {
-    const Resolved& R = gates[i];
-    qs_of[i].assign(R.t, R.t + R.k);
-    qs_of[i].insert(qs_of[i].end(), R.c, R.c + R.nc);
+    qs_of[i] = gate_qubits(gates[i]);
     for (int q : qs_of[i]) on_q[q].push_back(i);
   }
   std::vector<int> pos(n, 0);
@@ -272,31 +249,24 @@ void fuse_front(int n, const std::vector<Resolved>& gates, int kmax, std::vector
     for (int q : qs_of[i]) if (on_q[q][pos[q]] != i) return false;
     return true;
   };
-  auto take = [&](int i) {
+  auto take = [&](int i, Planned& b) {
     taken[i] = 1;
     for (int q : qs_of[i]) pos[q]++;
+    b.gates.push_back(i);
   };
   int next = 0;
   while (true) {
     while (next < G && taken[next]) next++;
     if (next >= G) break;
     const int seed = next;                       // all its predecessors are taken
+    Planned b;
+    b.q = qs_of[seed];
+    b.first = seed;
     if ((int)qs_of[seed].size() > kmax) {
-      take(seed);
-      Emitted e;
-      e.single = true;
-      e.gate = seed;
-      out.push_back(std::move(e));
+      take(seed, b);
+      out.push_back(std::move(b));
       continue;
     }
-    Block b;
-    b.ngates = 0;
-    for (int q : qs_of[seed]) {
-      Block id = single_qubit_identity(q);
-      if (b.q.empty()) { b.q = id.q; b.M = id.M; }
-      else kron_into(b, id);
-    }
-    b.first = seed;
     for (bool grown = true; grown;) {
       // every ready gate inside the block's qubits
       for (bool more = true; more;) {
@@ -306,10 +276,9 @@ void fuse_front(int n, const std::vector<Resolved>& gates, int kmax, std::vector
           while (pos[q] < (int)on_q[q].size()) {
             const int i = on_q[q][pos[q]];
             bool inside = ready(i);
-            for (int qq : qs_of[i]) if (inside && local_index(b, qq) < 0) inside = false;
+            for (int qq : qs_of[i]) if (inside && !has_qubit(b.q, qq)) inside = false;
             if (!inside) break;
-            block_apply(b, gates[i]);
-            take(i);
+            take(i, b);
             more = true;
           }
         }
@@ -323,20 +292,15 @@ void fuse_front(int n, const std::vector<Resolved>& gates, int kmax, std::vector
         const int i = on_q[q][pos[q]];
         if (!ready(i)) continue;
         int width = (int)b.q.size();
-        for (int qq : qs_of[i]) if (local_index(b, qq) < 0) width++;
+        for (int qq : qs_of[i]) if (!has_qubit(b.q, qq)) width++;
         if (width <= kmax && (best < 0 || i < best)) best = i;
       }
       if (best >= 0) {
-        for (int qq : qs_of[best])
-          if (local_index(b, qq) < 0) kron_into(b, single_qubit_identity(qq));
+        for (int qq : qs_of[best]) if (!has_qubit(b.q, qq)) b.q.push_back(qq);
         grown = true;
       }
     }
-    Emitted e;
-    e.single = (b.ngates == 1);
-    e.gate = seed;
-    if (!e.single) e.block = std::move(b);
-    out.push_back(std::move(e));
+    out.push_back(std::move(b));
   }
 }
 
@@ -344,73 +308,31 @@ void fuse_front(int n, const std::vector<Resolved>& gates, int kmax, std::vector
 // disjoint qubits (they commute with it) and joins the nearest earlier entry
 // whose union with it has at most kmax qubits; it stays where it is when it
 // reaches an entry it shares a qubit with and their union is wider.  Repeated
-// until nothing merges.  A merged entry is a dense block (left product in
-// FP64); unmerged single gates stay as they are, so structured kernels
-// (permutations, phases) keep serving them.
-void merge_pass(const std::vector<Resolved>& gates, int kmax, std::vector<Emitted>& em) {
-  auto qubits_of = [&](const Emitted& e) {
-    std::vector<int> qs;
-    if (e.single) {
-      const Resolved& R = gates[e.gate];
-      qs.assign(R.t, R.t + R.k);
-      qs.insert(qs.end(), R.c, R.c + R.nc);
-    } else {
-      qs = e.block.q;
-    }
-    return qs;
-  };
-  auto as_block = [&](const Emitted& e) {
-    if (!e.single) return e.block;
-    const Resolved& R = gates[e.gate];
-    Block b;
-    std::vector<int> qs(R.t, R.t + R.k);
-    qs.insert(qs.end(), R.c, R.c + R.nc);
-    for (int q : qs) {
-      Block id = single_qubit_identity(q);
-      if (b.q.empty()) { b.q = id.q; b.M = id.M; }
-      else kron_into(b, id);
-    }
-    block_apply(b, R);
-    b.first = e.gate;
-    return b;
-  };
+// until nothing merges.  A merged entry becomes a dense block; unmerged single
+// gates stay as they are, so structured kernels (permutations, phases) keep
+// serving them.
+void merge_pass(int kmax, std::vector<Planned>& em) {
   for (bool changed = true; changed;) {
     changed = false;
-    std::vector<Emitted> out;
-    std::vector<std::vector<int>> oq;   // qubits of each out entry
-    for (Emitted& e : em) {
-      const std::vector<int> qe = qubits_of(e);
+    std::vector<Planned> out;
+    for (Planned& e : em) {
       int target = -1;
       for (int i = (int)out.size() - 1; i >= 0; i--) {
-        int uni = (int)oq[i].size(), shared = 0;
-        for (int q : qe) {
-          if (std::find(oq[i].begin(), oq[i].end(), q) != oq[i].end()) shared++;
+        int uni = (int)out[i].q.size(), shared = 0;
+        for (int q : e.q) {
+          if (has_qubit(out[i].q, q)) shared++;
           else uni++;
         }
-        if ((int)qe.size() <= kmax && uni <= kmax) { target = i; break; }
+        if ((int)e.q.size() <= kmax && uni <= kmax) { target = i; break; }
         if (shared) break;
       }
       if (target < 0) {
-        oq.push_back(qe);
         out.push_back(std::move(e));
         continue;
       }
-      // out[target] then e, as one block on the union of their qubits
-      Block b = as_block(out[target]);
-      const Block be = as_block(e);
-      for (int q : be.q)
-        if (local_index(b, q) < 0) kron_into(b, single_qubit_identity(q));
-      Resolved R;
-      R.k = (int)be.q.size();
-      R.nc = 0;
-      for (int j = 0; j < R.k; j++) R.t[j] = be.q[j];
-      R.U = be.M;
-      const int ng = b.ngates + be.ngates;
-      block_apply(b, R);
-      b.ngates = ng;
-      out[target].single = false;
-      out[target].block = std::move(b);
-      oq[target] = out[target].block.q;
+      // out[target]'s gates, then e's (e commutes with every entry in between)
+      for (int q : e.q) if (!has_qubit(out[target].q, q)) out[target].q.push_back(q);
+      out[target].gates.insert(out[target].gates.end(), e.gates.begin(), e.gates.end());
       changed = true;
     }
     em.swap(out);
@@ -466,17 +388,23 @@ void emit_matrix_segment(int n, const std::vector<Resolved>& res, int begin, int
   if (begin >= end) return;
   std::vector<Resolved> seg(res.begin() + begin, res.begin() + end);
   // two planners, each followed by the merge pass; the plan with fewer sweeps
-  // is kept (ties: the first)
-  std::vector<Emitted> em, em2;
-  fuse(n, seg, std::min(fuse_k, n), em);
-  merge_pass(seg, std::min(fuse_k, n), em);
-  fuse_front(n, seg, std::min(fuse_k, n), em2);
-  merge_pass(seg, std::min(fuse_k, n), em2);
+  // is kept (ties: the first); only its blocks' matrices are built
+  const int kmax = std::min(fuse_k, n);
+  std::vector<Planned> em, em2;
+  fuse(n, seg, kmax, em);
+  merge_pass(kmax, em);
+  fuse_front(n, seg, kmax, em2);
+  merge_pass(kmax, em2);
   if (em2.size() < em.size()) em.swap(em2);
-  for (size_t i = 0; i < em.size(); i++) {
+  for (const Planned& p : em) {
     qc_op op;
-    if (em[i].single) { to_op(n, seg[em[i].gate], op); ops.push_back(op); continue; }
-    const Block& b = em[i].block;
+    if (p.gates.size() == 1) { to_op(n, seg[p.gates[0]], op); ops.push_back(op); continue; }
+    Block b;
+    b.q = p.q;
+    const size_t d = (size_t)1 << p.q.size();
+    b.M.assign(d * d, cd(0));
+    for (size_t i = 0; i < d; i++) b.M[i * d + i] = 1;
+    for (int g : p.gates) block_apply(b, seg[g]);
     Resolved R;
     R.k = (int)b.q.size();
     R.nc = 0;
