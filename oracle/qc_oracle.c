@@ -95,11 +95,3 @@ int orc_apply_gate(int n, cplx* psi, const cplx* U, const int* qubits, int k,
   }
   return 0;
 }
-
-/* <a|b> = sum conj(a_x) b_x, accumulated in FP64 (in a fixed serial order). */
-cplx orc_inner(int n, const cplx* a, const cplx* b) {
-  const int64_t N = (int64_t)1 << n;
-  cplx s = 0;
-  for (int64_t x = 0; x < N; x++) s += conj(a[x]) * b[x];
-  return s;
-}

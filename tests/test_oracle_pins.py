@@ -367,3 +367,85 @@ def test_tfxy_layout_follows_the_figure():
     blk = lambda i, j: [("X", (j,), (i,)), ("RX", (i,), ()), ("RZ", (j,), ()), ("X", (j,), (i,))]
     assert sig == rz(range(4)) + blk(0, 1) + blk(2, 3) + rz(range(4)) + blk(1, 2)
     assert [(x.name, x.qubits, tuple(x.controls)) for x in g[20:]] == sig
+
+
+# ----------------------------------------------------------- named gate matrices
+# The entries below are written out here, independently of oracle.gate_matrix:
+# Sec. 2.1's Clifford+T gates (S = diag(1, i), T = diag(1, e^{i pi/4})), the
+# Hadamard, and the readings P(theta) = diag(1, e^{i theta}),
+# R_P(theta) = exp(-i theta P / 2) of the gates the paper's circuits use.
+_R2 = 1.0 / math.sqrt(2.0)
+WRITTEN = {
+    "H": [[_R2, _R2], [_R2, -_R2]],
+    "X": [[0, 1], [1, 0]],
+    "Y": [[0, -1j], [1j, 0]],
+    "Z": [[1, 0], [0, -1]],
+    "S": [[1, 0], [0, 1j]],
+    "SDG": [[1, 0], [0, -1j]],
+    "T": [[1, 0], [0, _R2 + 1j * _R2]],
+    "TDG": [[1, 0], [0, _R2 - 1j * _R2]],
+}
+
+
+@pytest.mark.parametrize("name", sorted(WRITTEN))
+def test_fixed_gates_act_as_their_written_matrices(name):
+    """Every placement on a random 4-qubit state against I (x) M (x) I with
+    M's entries typed in above: a transposed, conjugated or mis-angled entry
+    (T = diag(1, e^{i pi/8}), S = diag(1, -i), ...) fails."""
+    M = np.array(WRITTEN[name], dtype=complex)
+    n = 4
+    rng = np.random.default_rng(80)
+    for q in range(n):
+        phi = rand_c(rng, 1 << n)
+        psi = phi.copy()
+        O.apply_gate(psi, n, Gate(name, (q,)))
+        ref = np.kron(np.kron(np.eye(1 << q), M), np.eye(1 << (n - q - 1))) @ phi
+        np.testing.assert_allclose(psi, ref, rtol=0, atol=1e-14)
+
+
+def test_clifford_t_relations():
+    """T^2 = S, S^2 = Z, S^dag S = T^dag T = I, H Z H = X, applied with the
+    oracle to a random state (each side a gate sequence)."""
+    n = 3
+    phi = C.random_state(n, 81)
+    rel = [(["T", "T"], ["S"]), (["S", "S"], ["Z"]), (["S", "SDG"], []), (["SDG", "S"], []),
+           (["T", "TDG"], []), (["TDG", "T"], []), (["H", "Z", "H"], ["X"]), (["T"] * 4, ["Z"])]
+    for lhs, rhs in rel:
+        for q in range(n):
+            a = O.run_circuit(n, [Gate(g, (q,)) for g in lhs], phi)
+            b = O.run_circuit(n, [Gate(g, (q,)) for g in rhs], phi)
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-15, err_msg="%s = %s" % (lhs, rhs))
+
+
+@pytest.mark.parametrize("name", ["RX", "RY", "RZ"])
+def test_rotations_are_exponentials_of_paulis(name):
+    """R_P(theta) = exp(-i theta P / 2) (reading C5) against a library matrix
+    exponential of the Pauli matrix typed in this file, for angles of both
+    signs -- a transposed rotation is R_P(-theta) and fails."""
+    from scipy.linalg import expm
+    P = PAULI[name[1]]
+    n = 3
+    rng = np.random.default_rng(82)
+    for t in (-2.5, -0.7, 0.3, 1.9, math.pi):
+        for q in range(n):
+            phi = rand_c(rng, 1 << n)
+            psi = phi.copy()
+            O.apply_gate(psi, n, Gate(name, (q,), theta=t))
+            M = expm(-0.5j * t * P)
+            ref = np.kron(np.kron(np.eye(1 << q), M), np.eye(1 << (n - q - 1))) @ phi
+            np.testing.assert_allclose(psi, ref, rtol=0, atol=1e-14)
+
+
+def test_rotation_amplitudes_on_basis_states():
+    """Amplitude by amplitude: RY(t)|0> = cos(t/2)|0> + sin(t/2)|1>,
+    RX(t)|0> = cos(t/2)|0> - i sin(t/2)|1>, RZ(t)|1> = e^{i t/2}|1>,
+    P(t)|1> = e^{i t}|1>."""
+    for t in (-2.0, -0.4, 0.9, 2.7):
+        c, s = math.cos(t / 2), math.sin(t / 2)
+        np.testing.assert_allclose(O.run_circuit(1, [Gate("RY", (0,), theta=t)]), [c, s], atol=1e-15)
+        np.testing.assert_allclose(O.run_circuit(1, [Gate("RX", (0,), theta=t)]), [c, -1j * s], atol=1e-15)
+        np.testing.assert_allclose(O.run_circuit(1, [Gate("RZ", (0,), theta=t)], O.basis_state(1, 1)),
+                                   [0, complex(c, s)], atol=1e-15)
+        np.testing.assert_allclose(O.run_circuit(1, [Gate("RZ", (0,), theta=t)]), [complex(c, -s), 0], atol=1e-15)
+        np.testing.assert_allclose(O.run_circuit(1, [Gate("P", (0,), theta=t)], O.basis_state(1, 1)),
+                                   [0, complex(math.cos(t), math.sin(t))], atol=1e-15)
