@@ -87,7 +87,8 @@ int qc_state_free(qc_state* s);
 /* Set the state to the computational basis state |x>, 0 <= x < 2^n. */
 int qc_state_set_basis(qc_state* s, uint64_t x);
 
-/* Copy all 2^n amplitudes device -> host (synchronous) or host -> device
+/* Copy all 2^n amplitudes device -> host (synchronous; QC_ERR_TIMEOUT as
+ * described at qc_device_status) or host -> device
  * (ordered on the state's stream; the host buffer must stay valid until the
  * stream reaches the copy when it is pinned, else the call is synchronous).
  * `host` holds 2^n interleaved (re, im) pairs of the state's element type. */
@@ -119,11 +120,33 @@ int qc_set_fused_tc(qc_state* s, int enable);
  * operations in the same order, so results are identical. */
 int qc_set_packed(qc_state* s, int enable);
 
-/* Device-side health counters: *tc_timeouts = number of tensor-core tile
- * waits that hit their iteration limit since the library was loaded (each
- * such wait sets the counter, abandons its tile and frees its tensor memory;
- * 0 in normal operation).  Synchronises the device. */
+/* Tensor-core waits.  A fused-block kernel on the tensor cores (qc_set_fused_tc)
+ * waits for its MMAs on an mbarrier with a poll limit.  A wait that reaches it
+ * counts on a per-device counter, stops the kernel from taking further tiles
+ * (the state is then incomplete) and, before the kernel frees its tensor
+ * memory, waits for the MMAs already committed (default limit).  The calls
+ * that synchronise -- qc_synchronize, qc_state_copy_to_host, qc_expect,
+ * qc_expect_noalloc and qc_apply_circuit with gate_ms -- return
+ * QC_ERR_TIMEOUT when the counter of the state's device is non-zero, and reset
+ * it: a wait that gave up in work on any state of that device is reported by
+ * the next such call.
+ *
+ * qc_device_status: *tc_timeouts = the current device's counter (0 in normal
+ * operation), not reset.  Ordered after work on the legacy default stream and
+ * on blocking streams, not after non-blocking streams: synchronise those
+ * first. */
 int qc_device_status(int* tc_timeouts);
+
+/* Wait for every call enqueued on the state's stream; QC_ERR_TIMEOUT as
+ * described above. */
+int qc_synchronize(const qc_state* s);
+
+/* Poll limit of the state's tensor-core MMA waits: polls > 0 sets it, 0
+ * restores the default (2^24 polls, seconds), polls < 0 makes every first
+ * wait give up without polling -- for testing the time-out path: the kernels
+ * stop after their first tile and the next synchronising call returns
+ * QC_ERR_TIMEOUT. */
+int qc_set_wait_limit(qc_state* s, long long polls);
 
 /* ---- single gates --------------------------------------------------------
  * qc_apply_1q: Sec. 2.1, Alg. 1.  U[8] = 2x2 complex row-major
@@ -361,9 +384,13 @@ int qc_expect_passes(int n, int dtype, const qc_pauli_sum* H, int* npasses);
  * 64 terms; larger sums return QC_ERR_ARG before any work is enqueued.
  * The first call on a device looks the array's device address up (with that
  * device current); make that first call before any stream capture.  Every
- * call uses the same array, so calls that overlap on the GPU (other threads,
- * other streams) race; calls from several host threads are serialised by the
- * library.  Synchronises the state's stream. */
+ * call in the process uses the same array and leaves its own sums in it.
+ * Calls whose work overlapped on the GPU would race on it; the library
+ * prevents that within a process by serialising the calls -- each holds a
+ * lock until its stream has finished -- so calls from several threads or on
+ * several streams run one after another.  Host memory for grouping the terms
+ * is the only memory the call takes.  Synchronises the state's stream
+ * (QC_ERR_TIMEOUT as described at qc_device_status). */
 int qc_expect_noalloc(const qc_state* s, const qc_pauli_sum* H, double* out);
 
 /* ---- gradients ------------------------------------------------------------

@@ -630,5 +630,6 @@ extern "C" int qc_apply_circuit(qc_state* s, const qc_gate* gates, int ngates, c
     }
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  if (o.gate_ms && rc == QC_OK) rc = qc_take_device_status("qc_apply_circuit");
   return rc;
 }

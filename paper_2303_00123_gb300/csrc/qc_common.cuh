@@ -23,6 +23,7 @@ struct qc_state {
   int device;           // CUDA device ordinal the memory lives on
   int fused_tc;         // 1: complex64 k-qubit blocks (k >= 3) on the tensor cores
   int packed;           // 1: float-float dense / phase sweeps use packed FP32 pairs
+  long long wait_limit; // tensor-core MMA wait limit in polls (0: default; < 0: no poll)
   cudaStream_t stream;  // work queue
 };
 
@@ -401,8 +402,13 @@ struct qc_op {
 // qubits, builds the matrix (host FP64) and converts qubits to bit positions.
 int qc_gate_to_op(int n, const qc_gate& g, qc_op& op);
 
-// Number of tensor-core tile waits that gave up (device counter; 0 normally).
+// Number of tensor-core tile waits that gave up on the current device and
+// have not been reported yet (device counter; 0 normally).
 int qc_tc_timeouts(int* count);
+// For calls that have just synchronised their stream: QC_ERR_TIMEOUT (and the
+// counter reset to 0) when a tensor-core wait on the current device gave up
+// since the last report, else QC_OK.
+int qc_take_device_status(const char* where);
 
 // Launch plan of a circuit: one op per gate, or per fused block (fuse_k >= 2);
 // with phase_runs, runs of commuting phase gates sharing a qubit become one

@@ -844,7 +844,7 @@ extern "C" int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out) 
   QC_CUDA(cudaMemcpyAsync(&result, partial + total, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   QC_CUDA(cudaStreamSynchronize(s->stream));
   *out = result;
-  return QC_OK;
+  return qc_take_device_status("qc_expect");
 }
 
 // ---------------------------------------------------------------------------
@@ -905,28 +905,23 @@ extern "C" int qc_expect_noalloc(const qc_state* s, const qc_pauli_sum* H, doubl
   if (!out) return qc_fail(QC_ERR_ARG, "out is NULL");
   if (!H || H->nterms < 0) return qc_fail(QC_ERR_ARG, "invalid Pauli sum");
   if (H->nterms > 0 && (!H->coeffs || !H->offsets)) return qc_fail(QC_ERR_ARG, "Pauli sum arrays are NULL");
-  // Validate every term and count the sweeps before touching the device.
-  int nsweeps = 0;
+  // Parse every term once (host memory only), then group the terms by flip
+  // mask: a stable sort keeps each group in term order.  One sweep per group
+  // and per kMaxTermsPerSweep terms of it.
+  struct NaTerm { uint64_t F, Q; int ny, t; };
+  std::vector<NaTerm> terms((size_t)H->nterms);
   for (int t = 0; t < H->nterms; t++) {
-    uint64_t F, Q;
-    int ny;
-    if (int rc = na_term(s->n, H, t, &F, &Q, &ny)) return rc;
-    bool seen = false;
-    for (int u = 0; u < t && !seen; u++) {
-      uint64_t F2, Q2;
-      int ny2;
-      na_term(s->n, H, u, &F2, &Q2, &ny2);
-      seen = (F2 == F);
-    }
-    if (seen) continue;
-    int cnt = 0;
-    for (int u = t; u < H->nterms; u++) {
-      uint64_t F2, Q2;
-      int ny2;
-      na_term(s->n, H, u, &F2, &Q2, &ny2);
-      if (F2 == F) cnt++;
-    }
-    nsweeps += (cnt + kMaxTermsPerSweep - 1) / kMaxTermsPerSweep;
+    NaTerm& x = terms[(size_t)t];
+    x.t = t;
+    if (int rc = na_term(s->n, H, t, &x.F, &x.Q, &x.ny)) return rc;
+  }
+  std::stable_sort(terms.begin(), terms.end(), [](const NaTerm& a, const NaTerm& b) { return a.F < b.F; });
+  int nsweeps = 0;
+  for (size_t a = 0; a < terms.size();) {
+    size_t b = a;
+    while (b < terms.size() && terms[b].F == terms[a].F) b++;
+    nsweeps += (int)((b - a + kMaxTermsPerSweep - 1) / kMaxTermsPerSweep);
+    a = b;
   }
   if (nsweeps > kNaSweeps)
     return qc_fail(QC_ERR_ARG, "qc_expect_noalloc: %d sweeps needed, the fixed scratch holds at most %d "
@@ -940,48 +935,32 @@ extern "C" int qc_expect_noalloc(const qc_state* s, const qc_pauli_sum* H, doubl
   const uint64_t N = 1ull << s->n;
   const int cap = std::min(qc_num_sms() * 8, kNaPartials);
   int sw = 0;
-  for (int t = 0; t < H->nterms; t++) {
-    uint64_t F, Q;
-    int ny;
-    na_term(s->n, H, t, &F, &Q, &ny);
-    bool seen = false;
-    for (int u = 0; u < t && !seen; u++) {
-      uint64_t F2, Q2;
-      int ny2;
-      na_term(s->n, H, u, &F2, &Q2, &ny2);
-      seen = (F2 == F);
-    }
-    if (seen) continue;
-    TermSet ts;
-    std::memset(&ts, 0, sizeof(ts));
-    ts.flip = F;
-    ts.pivot = F ? 63 - __builtin_clzll(F) : -1;
+  for (size_t a = 0; a < terms.size();) {
+    const uint64_t F = terms[a].F;
+    size_t b = a;
+    while (b < terms.size() && terms[b].F == F) b++;
     const uint64_t npairs = F ? N / 2 : N;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((npairs + kThreads - 1) / kThreads, cap));
-    for (int u = t; u <= H->nterms; u++) {
-      bool flush = (u == H->nterms);
-      if (!flush) {
-        uint64_t F2, Q2;
-        int ny2;
-        na_term(s->n, H, u, &F2, &Q2, &ny2);
-        if (F2 != F) continue;
-        ts.phase_mask[ts.nterms] = Q2;
-        ts.coeff[ts.nterms] = H->coeffs[u];
-        ts.ipow[ts.nterms] = ny2 & 3;
+    for (size_t c = a; c < b; c += kMaxTermsPerSweep) {
+      TermSet ts;
+      std::memset(&ts, 0, sizeof(ts));
+      ts.flip = F;
+      ts.pivot = F ? 63 - __builtin_clzll(F) : -1;
+      for (size_t u = c; u < b && ts.nterms < kMaxTermsPerSweep; u++) {
+        ts.phase_mask[ts.nterms] = terms[u].Q;
+        ts.coeff[ts.nterms] = H->coeffs[terms[u].t];
+        ts.ipow[ts.nterms] = terms[u].ny & 3;
         ts.nterms++;
-        flush = (ts.nterms == kMaxTermsPerSweep);
       }
-      if (flush && ts.nterms > 0) {
-        if (s->dtype == QC_C64)
-          k_pauli_sweep<float2><<<grid, kThreads, 0, s->stream>>>((const float2*)s->ptr, npairs, ts, partial);
-        else
-          k_pauli_sweep<double2><<<grid, kThreads, 0, s->stream>>>((const double2*)s->ptr, npairs, ts, partial);
-        k_sum_partials<<<1, kThreads, 0, s->stream>>>(partial, grid, sweep_sum + sw);
-        QC_LAUNCHED("qc_expect_noalloc sweep");
-        sw++;
-        ts.nterms = 0;
-      }
+      if (s->dtype == QC_C64)
+        k_pauli_sweep<float2><<<grid, kThreads, 0, s->stream>>>((const float2*)s->ptr, npairs, ts, partial);
+      else
+        k_pauli_sweep<double2><<<grid, kThreads, 0, s->stream>>>((const double2*)s->ptr, npairs, ts, partial);
+      k_sum_partials<<<1, kThreads, 0, s->stream>>>(partial, grid, sweep_sum + sw);
+      QC_LAUNCHED("qc_expect_noalloc sweep");
+      sw++;
     }
+    a = b;
   }
   double result = 0.0;
   if (sw > 0) {
@@ -991,5 +970,5 @@ extern "C" int qc_expect_noalloc(const qc_state* s, const qc_pauli_sum* H, doubl
   }
   QC_CUDA(cudaStreamSynchronize(s->stream));
   *out = result;
-  return QC_OK;
+  return qc_take_device_status("qc_expect_noalloc");
 }

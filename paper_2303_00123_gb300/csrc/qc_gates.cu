@@ -348,6 +348,20 @@ k_fused(vec32* __restrict__ st, const __grid_constant__ GeomF g, const __grid_co
 // next tile's inputs are loaded before the current tile's MMAs are awaited.
 static __device__ int g_tc_timeouts = 0;   // bounded mbarrier waits that gave up
 
+// Poll limits of the MMA completion waits.  A tile's wait gives up after
+// `spin` polls (kTcSpinDefault unless the state sets another limit); the
+// kernel then stops taking tiles and, before it frees its tensor memory,
+// waits for the MMAs it has committed with the default limit.
+constexpr int kTcSpinDefault = 1 << 24;
+
+__device__ __forceinline__ uint32_t mbar_poll(uint32_t mbar, uint32_t phase, int limit) {
+  uint32_t done = 0;
+  for (int it = 0; it < limit && !done; it++)
+    asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
+                 : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
+  return done;
+}
+
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -392,7 +406,7 @@ constexpr int kThreadsTC = 256;   // two threads per accumulator row, each owns 
 
 template <int K>
 __global__ void __launch_bounds__(kThreadsTC, 2)
-k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC64<K> U) {
+k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC64<K> U, int spin) {
   constexpr int D = 1 << K;
   constexpr int H = D / 2;                        // members per thread
   constexpr int KR = 2 * D;                       // GEMM N = K
@@ -454,7 +468,16 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
 #pragma unroll
     for (int r = 0; r < H; r++) x[r] = st[base + moff[r]];
   }
+  // bounded wait for the MMAs' completion; one decision for the CTA
   uint32_t phase = 0;
+  auto mma_wait = [&](int limit) {
+    uint32_t done = mbar_poll(mbar_a, phase, limit);
+    done = __syncthreads_and(done);   // tcgen05.ld is warp-collective
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (done) phase ^= 1u;
+    else if (t == 0) atomicAdd(&g_tc_timeouts, 1);
+    return done != 0;
+  };
   bool ok = true;
   for (; T < g.ntiles && ok; T += gridDim.x) {
     // split this thread's members into the A operands: Re -> column m0+r, Im -> column D+m0+r
@@ -511,17 +534,8 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
 #pragma unroll
       for (int r = 0; r < H; r++) x[r] = st[base + moff[r]];
     }
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; it++)
-      asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
-                   : "=r"(done) : "r"(mbar_a), "r"(phase) : "memory");
-    phase ^= 1u;
-    done = __syncthreads_and(done);   // one decision for the whole CTA (tcgen05.ld is warp-collective)
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!done) {
-      if (t == 0) atomicAdd(&g_tc_timeouts, 1);
-      ok = false;
-    } else {
+    ok = mma_wait(spin);
+    if (ok) {
       // accumulator row: columns m0..m0+H-1 = Re, D+m0.. = Im of this thread's outputs
       const uint32_t lane = tmem + ((uint32_t)(32 * (w & 3)) << 16);
       constexpr int NC = H < 16 ? H : 16;
@@ -543,6 +557,9 @@ k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __gri
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
+  // a wait gave up: its MMAs may still write tensor memory; wait for them (same
+  // phase, default limit) before freeing it
+  if (!ok) mma_wait(kTcSpinDefault);
   __syncthreads();
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL) : "memory");
 }
@@ -681,7 +698,7 @@ template <int K> struct Tc128Cfg {
 template <int K>
 __global__ void __launch_bounds__(Tc128Cfg<K>::NT, Tc128Cfg<K>::MINB)
 k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC128<K> U,
-              int eu, int sh) {
+              int eu, int sh, int spin) {
   constexpr int D = 1 << K;
   constexpr int TPR = Tc128Cfg<K>::TPR, NT = Tc128Cfg<K>::NT;
   constexpr int H = D / TPR;                      // members per thread
@@ -740,11 +757,8 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
   };
   // bounded wait for the MMAs' completion; one decision for the CTA
   uint32_t phase = 0;
-  auto mma_wait = [&]() {
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; it++)
-      asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
-                   : "=r"(done) : "r"(mbar_a), "r"(phase) : "memory");
+  auto mma_wait = [&](int limit) {
+    uint32_t done = mbar_poll(mbar_a, phase, limit);
     done = __syncthreads_and(done);   // tcgen05.ld is warp-collective
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (done) phase ^= 1u;
@@ -877,14 +891,15 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
 #pragma unroll
       for (int r = 0; r < H; r++) x[r] = st[base + moff[r]];
     }
-    ok = mma_wait();
+    ok = mma_wait(spin);
     if (ok) epilogue(cbase, cscale, cflush);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
-  // a wait gave up: its MMAs may still write tensor memory; wait once more (bounded) before freeing it
-  if (!ok) mma_wait();
+  // a wait gave up: its MMAs may still write tensor memory; wait for them (same
+  // phase, default limit) before freeing it
+  if (!ok) mma_wait(kTcSpinDefault);
   __syncthreads();
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL) : "memory");
 }
@@ -1389,12 +1404,13 @@ int launch_kq_t(qc_state* s, const qc_op& op) {
   MatD<Ar, D> M;
   for (int i = 0; i < D * D; i++) M.m[i] = Ar::make_coef(op.U[2 * i], op.U[2 * i + 1]);
   const size_t smem = (size_t)D * kThreadsK * sizeof(typename Ar::val_t);
-  static bool attr_set = false;   // per instantiation
-  if (!attr_set) {
+  static bool attr_set[64] = {};   // per instantiation and device (function attributes are per device)
+  const int dev = s->device;
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
     QC_CUDA(cudaFuncSetAttribute(k_kq<Ar, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     QC_CUDA(cudaFuncSetAttribute(k_kq<Ar, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared));
-    attr_set = true;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
   k_kq<Ar, K><<<grid_for(g.ngroups, kThreadsK), kThreadsK, smem, s->stream>>>((char*)s->ptr, g, M);
   QC_LAUNCHED("k_kq");
@@ -1488,12 +1504,13 @@ int launch_fused_t(qc_state* s, const qc_op& op, const GeomF& g, size_t smem) {
   constexpr int D = 1 << K;
   MatD<Ar, D> M;
   for (int i = 0; i < D * D; i++) M.m[i] = Ar::make_coef(op.U[2 * i], op.U[2 * i + 1]);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static bool attr_set[64] = {};   // per device
+  const int dev = s->device;
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
     QC_CUDA(cudaFuncSetAttribute(k_fused<Ar, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
     QC_CUDA(cudaFuncSetAttribute(k_fused<Ar, K>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared));
-    attr_set = true;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
   const uint64_t cap = (uint64_t)qc_num_sms() * 8;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
@@ -1519,13 +1536,22 @@ int launch_fused(qc_state* s, const qc_op& op, bool* done) {
 }
 
 
+// The state's MMA wait limit as a poll count (0 polls: every wait gives up at once).
+int tc_spin(const qc_state* s) {
+  if (s->wait_limit == 0) return kTcSpinDefault;
+  if (s->wait_limit < 0) return 0;
+  return (int)std::min<long long>(s->wait_limit, 1ll << 30);
+}
+
 template <int K>
 int launch_fused_tc_t(qc_state* s, const qc_op& op, const GeomF& g) {
   constexpr int D = 1 << K, KR = 2 * D;
   MatC64<K> U;
   for (int i = 0; i < D * D; i++) U.u[i] = make_float2((float)op.U[2 * i], (float)op.U[2 * i + 1]);
   const size_t smem = (size_t)2 * 128 * KR * 4 + (size_t)2 * KR * KR * 4;
-  static int per_sm = 0;
+  static int per_sm_dev[64] = {};   // per device (function attributes are per device)
+  const int sdev = s->device;
+  int per_sm = sdev >= 0 && sdev < 64 ? per_sm_dev[sdev] : 0;
   if (per_sm == 0) {
     QC_CUDA(cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // the default L1/shared split caps residency at one CTA per SM; ask for the full shared memory
@@ -1545,10 +1571,11 @@ int launch_fused_tc_t(qc_state* s, const qc_op& op, const GeomF& g) {
     const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
     const int ncol = 2 * KR < 32 ? 32 : 2 * KR;
     per_sm = std::max(1, std::min(std::min(by_regs, by_smem), std::min(512 / ncol, 2048 / kThreadsTC)));
+    if (sdev >= 0 && sdev < 64) per_sm_dev[sdev] = per_sm;
   }
   const uint64_t cap = (uint64_t)qc_num_sms() * per_sm;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
-  k_fused_tc<K><<<grid, kThreadsTC, smem, s->stream>>>((float2*)s->ptr, g, U);
+  k_fused_tc<K><<<grid, kThreadsTC, smem, s->stream>>>((float2*)s->ptr, g, U, tc_spin(s));
   QC_LAUNCHED("k_fused_tc");
   return QC_OK;
 }
@@ -1575,7 +1602,9 @@ int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
   }
   const int sh = S > 0.0 ? std::max(0, (int)std::ceil(std::log2(S * (1.0 + 0x1p-30))) + 4 - eu) : 0;
   const size_t smem = (size_t)kTcA * 128 * KR * 2 + (size_t)kTcB * KR * KR * 2;
-  static int per_sm = 0;
+  static int per_sm_dev[64] = {};   // per device (function attributes are per device)
+  const int sdev = s->device;
+  int per_sm = sdev >= 0 && sdev < 64 ? per_sm_dev[sdev] : 0;
   if (per_sm == 0) {
     QC_CUDA(cudaFuncSetAttribute(k_fused_tc128<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     QC_CUDA(cudaFuncSetAttribute(k_fused_tc128<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1592,10 +1621,11 @@ int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
     const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
     const int ncol = kTcLev * KR <= 128 ? 128 : (kTcLev * KR <= 256 ? 256 : 512);
     per_sm = std::max(1, std::min(std::min(by_regs, by_smem), std::min(512 / ncol, 2048 / NT)));
+    if (sdev >= 0 && sdev < 64) per_sm_dev[sdev] = per_sm;
   }
   const uint64_t cap = (uint64_t)qc_num_sms() * per_sm;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
-  k_fused_tc128<K><<<grid, Tc128Cfg<K>::NT, smem, s->stream>>>((double2*)s->ptr, g, U, eu, sh);
+  k_fused_tc128<K><<<grid, Tc128Cfg<K>::NT, smem, s->stream>>>((double2*)s->ptr, g, U, eu, sh, tc_spin(s));
   QC_LAUNCHED("k_fused_tc128");
   return QC_OK;
 }
@@ -1893,6 +1923,16 @@ int dispatch(qc_state* s, qc_op op) {
 int qc_tc_timeouts(int* count) {
   QC_CUDA(cudaMemcpyFromSymbol(count, g_tc_timeouts, sizeof(int)));
   return QC_OK;
+}
+
+int qc_take_device_status(const char* where) {
+  int count = 0;
+  if (int rc = qc_tc_timeouts(&count)) return rc;
+  if (count == 0) return QC_OK;
+  const int zero = 0;
+  QC_CUDA(cudaMemcpyToSymbol(g_tc_timeouts, &zero, sizeof(int)));
+  return qc_fail(QC_ERR_TIMEOUT, "%s: %d tensor-core wait(s) on this device gave up; the states they "
+                 "were updating are incomplete", where, count);
 }
 
 int qc_launch_op(qc_state* s, const qc_op& op) {

@@ -49,15 +49,13 @@ int qc_cuda_fail(cudaError_t e, const char* what) {
 }
 
 int qc_num_sms() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-      sms = v;
-    else
-      return 132;
-  }
-  return sms;
+  static int sms[64] = {0};   // per device ordinal
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 132;
+  if (dev >= 0 && dev < 64 && sms[dev] > 0) return sms[dev];
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 132;
+  if (dev >= 0 && dev < 64) sms[dev] = v;
+  return v;
 }
 
 int qc_check_state(const qc_state* s) {
@@ -85,6 +83,7 @@ static int new_handle(void* ptr, int n, int dtype, int owned, qc_state** out) {
   s->arith = QC_ARITH_AUTO;
   s->fused_tc = 1;
   s->packed = 1;
+  s->wait_limit = 0;
   s->stream = nullptr;
   cudaGetDevice(&s->device);
   *out = s;
@@ -161,6 +160,18 @@ int qc_state_copy_to_host(const qc_state* s, void* host) {
   const size_t bytes = ((size_t)1 << s->n) * elem_size(s->dtype);
   QC_CUDA(cudaMemcpyAsync(host, s->ptr, bytes, cudaMemcpyDeviceToHost, s->stream));
   QC_CUDA(cudaStreamSynchronize(s->stream));
+  return qc_take_device_status("qc_state_copy_to_host");
+}
+
+int qc_synchronize(const qc_state* s) {
+  if (int rc = qc_check_state(s)) return rc;
+  QC_CUDA(cudaStreamSynchronize(s->stream));
+  return qc_take_device_status("qc_synchronize");
+}
+
+int qc_set_wait_limit(qc_state* s, long long polls) {
+  if (!s) return qc_fail(QC_ERR_ARG, "state handle is NULL");
+  s->wait_limit = polls;
   return QC_OK;
 }
 

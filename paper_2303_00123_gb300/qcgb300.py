@@ -95,6 +95,8 @@ def _load():
         "qc_set_fused_tc": [P, I],
         "qc_set_packed": [P, I],
         "qc_device_status": [IP],
+        "qc_synchronize": [P],
+        "qc_set_wait_limit": [P, ctypes.c_longlong],
         "qc_apply_1q": [P, DP, I],
         "qc_apply_c1q": [P, DP, IP, IP, I, I],
         "qc_apply_2q": [P, DP, I, I],
@@ -266,6 +268,15 @@ class State:
     def set_packed(self, enable: bool):
         """complex128 float-float sweeps with packed FP32 pairs (default) or scalar."""
         _check(lib.qc_set_packed(self._h, int(bool(enable))))
+
+    def set_wait_limit(self, polls: int):
+        """Tensor-core MMA wait limit in polls (0: default; < 0: no poll, for tests)."""
+        _check(lib.qc_set_wait_limit(self._h, int(polls)))
+
+    def synchronize(self):
+        """Wait for the state's stream; raises QCError(QC_ERR_TIMEOUT) when a
+        tensor-core wait on its device gave up since the last report."""
+        _check(lib.qc_synchronize(self._h))
 
     def set_basis(self, x: int = 0):
         _check(lib.qc_state_set_basis(self._h, ctypes.c_uint64(x)))

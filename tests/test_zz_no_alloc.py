@@ -6,14 +6,16 @@ latency-critical loop): it keeps its partial sums in a fixed array in the
 library's device code.  This test calls it twice in a row on the same states
 -- the second call reuses the array as the first left it -- and checks both
 results against the allocating entry point, within the expectation-value
-tolerances of the other GPU tests.  It also checks that a sum needing more
-sweeps than the fixed array holds is rejected without running.
+tolerances of the other GPU tests, and against the FP64 oracle's value for
+the same circuit.  It also checks that a sum needing more sweeps than the
+fixed array holds is rejected without running.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2303_00123_gb300 import circuits as C
 
 pytestmark = pytest.mark.gpu
@@ -42,7 +44,9 @@ def call_noalloc(q, st, H):
 def test_noalloc_matches_allocating_expect_twice(q, dtype, tol):
     n = 12
     st = q.State(n, q.C128 if dtype == "c128" else q.C64)
-    st.apply_circuit(C.random_mix(n, 120, seed=44))
+    gates = C.random_mix(n, 120, seed=44)
+    st.apply_circuit(gates)
+    psi = O.run_circuit(n, gates)
     H1 = C.tfim(n, 0.9) + [(0.3, [("Y", 1), ("X", 3)]), (-0.2, [("Y", 0), ("Z", 2), ("Y", 11)]), (0.5, [])]
     H2 = [(1.0, [("Z", i)]) for i in range(n)] + [(0.25, [("X", i), ("X", (i + 1) % n)]) for i in range(n)]
     for H in (H1, H2):
@@ -53,6 +57,8 @@ def test_noalloc_matches_allocating_expect_twice(q, dtype, tol):
         # complex64: qc_expect forms FP32 in-tile partial sums (bound 2e-6 * sum|c|)
         t = tol * (1.0 if dtype == "c128" else max(1.0, sum(abs(c) for c, _ in H)))
         assert abs(v1 - ref) <= t and abs(v2 - ref) <= t
+        # against the oracle: complex128 1e-10, complex64 state with FP64 reductions 2e-4
+        assert abs(v1 - O.expect(psi, n, H)) <= (1e-10 if dtype == "c128" else 2e-4)
     st.free()
 
 
