@@ -163,20 +163,70 @@ def profiled_traffic():
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_oracle_sample(n_gates_each=6):
-    """Oracle (FP64 C, OpenMP) on the first gates of both circuits at n=30."""
-    from oracle import oracle as O
+def gate_class(g):
+    """Cost class of a gate for extrapolating oracle timings."""
+    name = g.name.upper()
+    if name == "SWAP":
+        return "swap"
+    if g.controls:
+        return "controlled"
+    return "one_qubit"
+
+
+def oracle_sample_gates():
+    """40 gates of the step that cover every gate class: the first 14 and the
+    last 3 (SWAP) of the QFT, the first 20 Haar U(2) and 3 CNOTs of the brickwork."""
     x, qft, brick = workload()
-    sample = qft[:n_gates_each] + brick[:n_gates_each]
+    cnots = [g for g in brick if g.controls][:3]
+    return x, qft[:14] + qft[-3:] + brick[:20] + cnots, qft + brick
+
+
+def cpu_oracle_sample():
+    """The FP64 oracle (C, OpenMP over the host cores) on 40 gates of the step
+    at n=30, extrapolated to the whole step per gate class; plus the oracle on
+    one thread for two gates (a U(2) and a controlled phase), scaled by class."""
+    from oracle import oracle as O
+    x, sample, full = oracle_sample_gates()
     psi = O.basis_state(N_QUBITS, x)
-    t0 = time.perf_counter()
+    per = {}
+    t_all = time.perf_counter()
     for g in sample:
+        t0 = time.perf_counter()
         O.apply_gate(psi, N_QUBITS, g)
-    dt = time.perf_counter() - t0
+        per.setdefault(gate_class(g), []).append(time.perf_counter() - t0)
+    dt = time.perf_counter() - t_all
+    del psi
+    cls_s = {c: float(np.mean(v)) for c, v in per.items()}
+    step_s = sum(cls_s[gate_class(g)] for g in full)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": len(sample) / dt, "unit": "gates/s", "cores": cores, "kind": "oracle",
-            "sample": "first %d gates of the QFT and of the brickwork circuit at n=%d complex128 "
-                      "(%d gates, %.1f s)" % (n_gates_each, N_QUBITS, len(sample), dt)}
+    out = {"value": round(len(full) / step_s, 4), "unit": "gates/s", "cores": cores, "kind": "oracle",
+           "sample": "40 of the step's gates at n=%d complex128 (QFT: first 14 and the 3 last SWAPs; brickwork: "
+                     "first 20 U(2) and 3 CNOTs), %.1f s, extrapolated to the %d-gate step per gate class"
+                     % (N_QUBITS, dt, len(full)),
+           "sample_gates_per_s": round(len(sample) / dt, 4),
+           "s_per_gate_by_class": {c: round(v, 4) for c, v in cls_s.items()}}
+    # single thread: the oracle library reads OMP_NUM_THREADS at load; run it in a child process
+    code = ("import sys, time, json; sys.path.insert(0, %r); import bench; from oracle import oracle as O;"
+            "x, sample, full = bench.oracle_sample_gates(); g1 = [g for g in sample if bench.gate_class(g) == "
+            "'one_qubit'][0]; g2 = [g for g in sample if bench.gate_class(g) == 'controlled'][0];"
+            "psi = O.basis_state(bench.N_QUBITS, x); r = {};"
+            "t0 = time.perf_counter(); O.apply_gate(psi, bench.N_QUBITS, g1); r['one_qubit'] = time.perf_counter() - t0;"
+            "t0 = time.perf_counter(); O.apply_gate(psi, bench.N_QUBITS, g2); r['controlled'] = time.perf_counter() - t0;"
+            "print(json.dumps(r))" % ROOT)
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        # classes not timed on one thread take the multithreaded ratio of the U(2) gate
+        ratio = one["one_qubit"] / cls_s["one_qubit"]
+        st_s = sum(one.get(gate_class(g), cls_s[gate_class(g)] * ratio) for g in full)
+        out["single_thread"] = {"value": round(len(full) / st_s, 5), "unit": "gates/s", "cores": 1,
+                                "sample": "one U(2) and one controlled phase at n=30 on one thread, "
+                                          "extrapolated to the step per gate class",
+                                "s_per_gate_by_class": {c: round(v, 3) for c, v in one.items()}}
+    except Exception as e:  # noqa: BLE001 -- the multithreaded figure stands alone
+        out["single_thread"] = {"unavailable": str(e)[:200]}
+    return out
 
 
 def workload_config(args, world, gates_per_step):
@@ -188,6 +238,23 @@ def workload_config(args, world, gates_per_step):
 
 
 # ---------------------------------------------------------------- GPU arm
+E2E_MAX_STEPS = 3        # the end-to-end loop repeats at most this many steps
+
+
+def dense_roofline(ms_list, bytes_total, peak, peak_kind, label, traffic=None):
+    """Roofline of the dense 1-qubit sweep from per-launch CUDA-event times."""
+    if not ms_list:
+        return None
+    per_launch_bytes = bytes_total / len(ms_list)
+    avg_ms = float(np.mean(ms_list))
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": label,
+            "peak_kind": peak_kind + " (copy bandwidth, MEASURED_PEAKS.json)",
+            "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": round(avg_ms, 4),
+            "launches": len(ms_list)}
+
+
 def run_gpu(args):
     import torch
     from paper_2303_00123_gb300 import qcgb300 as q
@@ -205,15 +272,17 @@ def run_gpu(args):
     gates_per_step = len(qft) + len(brick)
     t = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
     st = q.State.from_tensor(t)
-    st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
+    arith = q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE
+    st.set_arith(arith)
     stream = torch.cuda.Stream()
     st.set_stream(stream)
     elem = 16
 
     dense_ms, dense_bytes = [], 0.0
+    per_q = {}
     launches = 0
 
-    def step(record):
+    def step(record, sink=None):
         nonlocal launches, dense_bytes
         for circ in (qft, brick):
             st.set_basis(x)
@@ -222,8 +291,10 @@ def run_gpu(args):
             if record and args.fuse == 0:
                 for g, m in zip(circ, ms):
                     if g.name.upper() == "U" and not g.controls:
-                        dense_ms.append(m)
-                        dense_bytes += algorithmic_bytes(g, n, elem)
+                        (sink if sink is not None else dense_ms).append(m)
+                        if sink is None:
+                            dense_bytes += algorithmic_bytes(g, n, elem)
+                            per_q.setdefault(g.qubits[0], []).append(m)
 
     for _ in range(args.warmup):
         step(False)
@@ -244,17 +315,35 @@ def run_gpu(args):
     elapsed, value = aggregate_ranks(elapsed, gates_per_step * args.steps, dist, "cuda")
 
     peak, peak_kind = measured_peaks()
-    roof = None
-    if dense_ms:
-        per_launch_bytes = dense_bytes / len(dense_ms)
-        avg_ms = float(np.mean(dense_ms))
-        achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
-                "kernel": "k_dense (1-qubit Haar U(2), complex128, %s)" % args.arith,
-                "peak_kind": peak_kind + " (copy bandwidth, MEASURED_PEAKS.json)",
-                "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": round(avg_ms, 4),
-                "launches": len(dense_ms)}
+    roof = dense_roofline(dense_ms, dense_bytes, peak, peak_kind,
+                          "k_dense (1-qubit Haar U(2), complex128, %s)" % args.arith, profiled_traffic())
+    per_target = None
+    if per_q:
+        ub = 2 * (1 << n) * elem
+        per_target = {"what": "dense 1-qubit Haar U(2) sweeps of the brickwork, by target qubit q (stride 2^(29-q) "
+                              "amplitudes): average GB/s of algorithmic bytes",
+                      "q": sorted(per_q), "GBps": [round(ub / (float(np.mean(per_q[k])) * 1e-3) / 1e9, 1)
+                                                   for k in sorted(per_q)]}
+
+    # the same step in native FP64 arithmetic (one timed step, outside the timed region)
+    native = None
+    if not args.no_native and args.arith == "f32x2" and args.fuse == 0:
+        st.set_arith(q.ARITH_NATIVE)
+        step(False)
+        nat_ms = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step(True, sink=nat_ms)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        nat_s = e0.elapsed_time(e1) / 1e3
+        st.set_arith(arith)
+        native = {"value": round(gates_per_step / nat_s, 3), "unit": "gates/s", "dtype": "c128-f64",
+                  "ms_per_step": round(nat_s * 1e3, 1), "steps": 1,
+                  "roofline": dense_roofline(nat_ms, 2 * (1 << n) * elem * len(nat_ms), peak, peak_kind,
+                                             "k_dense (1-qubit Haar U(2), complex128, native FP64)"),
+                  "note": "the same step with QC_ARITH_NATIVE: plain FP64 arithmetic (GB300 FP64 FMA ~1/64 of FP32)"}
 
     # e2e through the C ABI with pinned host buffers: the input state (prepared once) is
     # copied host->device for every circuit, the final state device->host into a second buffer
@@ -264,31 +353,60 @@ def run_gpu(args):
         host_in[x] = 1.0
         host_out = torch.empty(1 << n, dtype=torch.complex128, pin_memory=True)
         in_np, out_np = host_in.numpy(), host_out.numpy()
+        e2e_steps = max(1, min(args.steps, E2E_MAX_STEPS))
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(2 * e2e_steps)]
+        enqueue_s = 0.0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            for circ in (qft, brick):
+        for i in range(e2e_steps):
+            for c, circ in enumerate((qft, brick)):
+                ev = evs[2 * i + c]
+                ev[0].record(stream)
                 q.lib.qc_state_copy_from_host(st.handle, q.ctypes.c_void_p(in_np.ctypes.data))
+                ev[1].record(stream)
+                ta = time.perf_counter()
                 st.apply_circuit(circ, fuse_k=args.fuse)
+                enqueue_s += time.perf_counter() - ta
+                ev[2].record(stream)
                 st.to_numpy(out=out_np)     # device->host copy of the final state (synchronises)
+                ev[3].record(stream)
         e2e_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        h2d = sum(e[0].elapsed_time(e[1]) for e in evs) / e2e_steps
+        circ_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / e2e_steps
+        d2h = sum(e[2].elapsed_time(e[3]) for e in evs) / e2e_steps
+        wall = e2e_s / e2e_steps * 1e3
         del host_in, host_out, in_np, out_np
         bi = 2 * (1 << n) * elem
-        e2e = {"value": gates_per_step * args.steps * world / e2e_s, "unit": "gates/s",
-               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi}
+        e2e = {"value": gates_per_step * e2e_steps * world / e2e_s, "unit": "gates/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi, "steps": e2e_steps,
+               "breakdown_ms_per_step": {
+                   "wall": round(wall, 1), "h2d": round(h2d, 1), "circuits": round(circ_ms, 1), "d2h": round(d2h, 1),
+                   "host_enqueue": round(enqueue_s / e2e_steps * 1e3, 1),
+                   "other": round(wall - h2d - circ_ms - d2h, 1),
+                   "note": "h2d, circuits, d2h: CUDA events on the state's stream around each phase (two circuits "
+                           "per step); host_enqueue: wall time of the apply calls (marshalling, planning, launches, "
+                           "overlapping the device work); other = wall - h2d - circuits - d2h"}}
 
-    extras = {} if args.no_extras else extra_measurements(q, st, stream, brick, x)
+    extras = {} if args.no_extras else extra_measurements(q, st, stream, brick, x, args)
     line = {
         "metric": "gates/s at n=30 complex128 (QFT 480 + brickwork depth-40 1780 gates, unfused)",
         "value": round(value, 3), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed / args.steps * 1e3, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128-" + args.arith, "data": "synthetic",
+        "arith_note": ("complex128 state (IEEE binary64 in HBM); each gate computed in float-float on the FP32 pipes "
+                       "(47-bit significands, inputs below 2^-100 flushed); native_fp64 below is the same step in "
+                       "plain FP64" if args.arith == "f32x2" else "plain FP64 arithmetic"),
         "config": workload_config(args, world, gates_per_step),
         "gpu_launches": launches,
         "roofline": roof,
         "e2e": e2e,
         "clocks": clk.summary(),
     }
+    if native:
+        line["native_fp64"] = native
+    if per_target:
+        line["per_target"] = per_target
     line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample()
@@ -574,21 +692,87 @@ def _event_ms(stream, fn, reps=1):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_measurements(q, st, stream, brick, x):
+def fusion_sweep(q, stream, brick, peak):
+    """Brickwork depth 40 fused into k-qubit blocks: n=30 complex128 and
+    complex64 at k = 0 (gate by gate), 2, 3, 4, 5; n=32 at k = 5; amplitude
+    error against the FP64 oracle at n=20 for every k.  Tensor-core blocks
+    (k >= 3): algorithmic flops 8 * 2^k per amplitude and block over the
+    tensor peak of the operand type (tf32 = bf16 / 2, fp16 = bf16, nominal
+    ratios), beside the HBM fraction."""
+    import torch
+    from oracle import oracle as O
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    out = {}
+    # warm every kernel shape on a small state first (function attributes, first launches)
+    for dt in (q.C128, q.C64):
+        sw = q.State(20, dt)
+        sw.set_stream(stream)
+        for k in (0, 2, 3, 4, 5):
+            sw.set_basis(0)
+            sw.apply_circuit(C.brickwork(20, 4, seed=1), fuse_k=k)
+        sw.free()
+    for n, ks in ((N_QUBITS, (0, 2, 3, 4, 5)), (32, (5,))):
+        circ = brick if n == N_QUBITS else C.brickwork(n, BRICK_DEPTH, seed=SEED_BRICK)
+        for dname, dt, elem, tdt in (("c128", q.C128, 16, torch.complex128), ("c64", q.C64, 8, torch.complex64)):
+            t = torch.empty(1 << n, dtype=tdt, device="cuda")
+            s2 = q.State.from_tensor(t)
+            s2.set_stream(stream)
+            res = {}
+            for k in ks:
+                def run():
+                    s2.set_basis(0)
+                    s2.apply_circuit(circ, fuse_k=k)
+                ms = _event_ms(stream, run)
+                plan = q.fuse_plan(n, circ, k) if k else None
+                nl = len(plan) if k else len(circ)
+                nblk = sum(1 for b in plan if not isinstance(b[0], str) and len(b[0]) >= 3) if k >= 3 else 0
+                if k:   # a block sweep moves 2 N E bytes (halved per control)
+                    byts = sum(2 * (1 << n) * elem / (1 << len(b[1])) if not isinstance(b[0], str)
+                               else 2 * (1 << n) * elem for b in plan)
+                else:
+                    byts = sum(algorithmic_bytes(gt, n, elem) for gt in circ)
+                hbm = byts / (ms * 1e-3) / 1e9
+                r = {"ms": round(ms, 1), "launches": nl, "gates_per_s": round(len(circ) / ms * 1e3, 1),
+                     "eff_GBps": round(hbm, 1), "hbm_frac": round(hbm / peak, 4)}
+                if nblk:
+                    tpeak = bf16 / 2 if dt == q.C64 else bf16
+                    tf = nblk * 8 * (1 << k) * (1 << n) / (ms * 1e-3) / 1e12
+                    r["tensor"] = {"blocks": nblk, "TFLOPs": round(tf, 1), "peak": round(tpeak, 1),
+                                   "frac": round(tf / tpeak, 4),
+                                   "op": "tf32 split (3 products)" if dt == q.C64 else "fp16 digit slices (27 products)"}
+                res[str(k)] = r
+            if "0" in res:
+                res["speedup_k5"] = round(res["0"]["ms"] / res["5"]["ms"], 2)
+            out["n%d_%s" % (n, dname)] = res
+            s2.free()
+            del t
+            torch.cuda.empty_cache()
+    # accuracy at n=20 against the FP64 oracle (same circuit family)
+    ne = 20
+    g2 = C.brickwork(ne, BRICK_DEPTH, seed=SEED_BRICK)
+    ref = O.run_circuit(ne, g2)
+    err = {}
+    for dname, dt in (("c128", q.C128), ("c64", q.C64)):
+        for k in (0, 2, 3, 4, 5):
+            s3 = q.State(ne, dt)
+            s3.apply_circuit(g2, fuse_k=k)
+            got = s3.to_numpy().astype(np.complex128)
+            s3.free()
+            err["%s_k%d" % (dname, k)] = {"max_abs": float(np.max(np.abs(got - ref))),
+                                           "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+    out["error_vs_oracle_n20"] = err
+    return out
+
+
+def extra_measurements(q, st, stream, brick, x, args):
     """Fused, batched and adjoint forms against the plain per-gate form, on
     this GPU, outside the main timed region (each reported with its config)."""
     import torch
     out = {}
-    # fused brickwork (n=30): complex128 and complex64 k=5 blocks on the tensor cores
-    fused = {}
-    def brick_run(state, k):
-        state.set_basis(0)
-        state.apply_circuit(brick, fuse_k=k)
-    brick_run(st, 5)
-    t0 = _event_ms(stream, lambda: brick_run(st, 0))
-    t5 = _event_ms(stream, lambda: brick_run(st, 5))
-    fused["c128_k5_tensor_cores"] = {"ms": round(t5, 1), "unfused_ms": round(t0, 1), "speedup": round(t0 / t5, 2),
-                                     "launches": len(q.fuse_plan(N_QUBITS, brick, 5))}
+    peak, _ = measured_peaks()
+    fused = {"brickwork": fusion_sweep(q, stream, brick, peak)}
     qft = C.qft(N_QUBITS)
     def qft_run(k):
         st.set_basis(x)
@@ -622,11 +806,6 @@ def extra_measurements(q, st, stream, brick, x):
     t64 = torch.empty(1 << N_QUBITS, dtype=torch.complex64, device="cuda")
     s64 = q.State.from_tensor(t64)
     s64.set_stream(stream)
-    brick_run(s64, 5)
-    u0 = _event_ms(stream, lambda: brick_run(s64, 0))
-    u5 = _event_ms(stream, lambda: brick_run(s64, 5))
-    fused["c64_k5_tensor_cores"] = {"ms": round(u5, 1), "unfused_ms": round(u0, 1), "speedup": round(u0 / u5, 2),
-                                    "launches": len(q.fuse_plan(N_QUBITS, brick, 5))}
     # TFXY Trotter circuit (Sec. 4, 10 steps): complex128 k=2, complex64 k=5 on the tensor cores
     tfxy = C.tfxy_trotter(N_QUBITS, TFXY_STEPS, seed=SEED_TFXY)
     def tfxy_run(state, k):
@@ -645,8 +824,10 @@ def extra_measurements(q, st, stream, brick, x):
     wk = _event_ms(stream, lambda: tfxy_run(st, TFXY_C128_K))
     fused["tfxy_c128_k%d" % TFXY_C128_K] = {"ms": round(wk, 1), "unfused_ms": round(w0, 1), "speedup": round(w0 / wk, 2),
                                             "launches": len(q.fuse_plan(N_QUBITS, tfxy, TFXY_C128_K))}
-    out["fused"] = {"workload": "n=30: brickwork depth 40 (greedy k-qubit blocks); QFT (each H merged with its "
-                                "phase run, final SWAPs as one bit permutation); TFXY Trotter, 10 steps", **fused}
+    out["fused"] = {"workload": "brickwork depth 40 (greedy k-qubit blocks) at n=30 (k=0,2..5) and n=32 (k=5), "
+                                "complex128 and complex64, error vs the FP64 oracle at n=20; n=30 QFT (each H merged "
+                                "with its phase run, final SWAPs as one bit permutation); n=30 TFXY Trotter, 10 steps",
+                    **fused}
     # batched: 1024 circuits, one persistent launch vs one launch per gate
     specs = C.batch_specs(1024, seed=4)
     circs = [C.random_mix(n, d, seed=sd) for n, d, sd in specs]
@@ -705,31 +886,48 @@ def extra_measurements(q, st, stream, brick, x):
 
 
 def run_reference(args):
+    """The oracle as it stands, on the host cores: each step applies 6 gates of
+    the 40-gate sample (in turn) to the n=30 state; `value` extrapolates the
+    per-class times to the whole 2260-gate step."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import oracle as O
-    x, qft, brick = workload()
-    sample = qft[:3] + brick[:3]
+    x, sample, full = oracle_sample_gates()
     psi = O.basis_state(N_QUBITS, x)
-    for _ in range(args.warmup):
-        O.apply_gate(psi, N_QUBITS, sample[0])
-    t0 = time.perf_counter()
+    for i in range(args.warmup):
+        O.apply_gate(psi, N_QUBITS, sample[i % len(sample)])
+    per = {}
+    t_all = time.perf_counter()
+    k = 0
     for _ in range(args.steps):
-        for g in sample:
+        for _ in range(6):
+            g = sample[k % len(sample)]
+            k += 1
+            t0 = time.perf_counter()
             O.apply_gate(psi, N_QUBITS, g)
-    dt = time.perf_counter() - t0
-    value = len(sample) * args.steps / dt
+            per.setdefault(gate_class(g), []).append(time.perf_counter() - t0)
+    dt = time.perf_counter() - t_all
+    cls_s = {c: float(np.mean(v)) for c, v in per.items()}
+    # classes the steps did not reach take the U(2) time (the costliest class)
+    step_s = sum(cls_s.get(gate_class(g), cls_s.get("one_qubit", max(cls_s.values()))) for g in full)
+    value = len(full) / step_s
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    cpu = {"value": value, "unit": "gates/s", "cores": cores, "kind": "oracle",
-           "sample": "each step: first 3 gates of the QFT and of the brickwork circuit at n=30 complex128"}
+    cpu = {"value": round(value, 4), "unit": "gates/s", "cores": cores, "kind": "oracle",
+           "sample": "each step: 6 gates of a 40-gate sample of the n=30 complex128 step (QFT: first 14 and last 3 "
+                     "SWAPs; brickwork: first 20 U(2), 3 CNOTs), taken in turn; extrapolated to the %d-gate step "
+                     "per gate class" % len(full),
+           "sample_gates_per_s": round(6 * args.steps / dt, 4)}
+    cfg = workload_config(args, world, len(full))
+    cfg["arith"] = "f64 (FP64 CPU oracle)"
+    cfg["fuse_k"] = 0
     print(json.dumps({
         "impl": "reference", "metric": "gates/s at n=30 complex128 (QFT 480 + brickwork depth-40 1780 gates, unfused)",
         "value": round(value, 4), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, world, len(qft) + len(brick)),
+        "config": cfg,
         "cpu_baseline": cpu, "e2e": {"value": round(value, 4), "unit": "gates/s", "h2d_bytes_per_step": 0,
                                      "d2h_bytes_per_step": 0}}))
 
@@ -744,6 +942,8 @@ def main():
     ap.add_argument("--fuse", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-native", dest="no_native", action="store_true",
+                    help="skip the native-FP64 step beside the float-float headline")
     ap.add_argument("--no-extras", dest="no_extras", action="store_true",
                     help="skip the fused / batched / adjoint side measurements")
     ap.add_argument("--case", default=None, help="micro-benchmark: dense1q, dense2q, cnot, cphase, swap, h")
@@ -755,6 +955,18 @@ def main():
     ap.add_argument("--no-tc", dest="no_tc", action="store_true", help="complex64 blocks on CUDA cores")
     ap.add_argument("--no-packed", dest="no_packed", action="store_true", help="scalar FP32 float-float")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and not args.case:
+        # one replica rank per GPU, launched here when no launcher set the ranks up
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(args.gpus),
+               "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+        raise SystemExit(subprocess.call(cmd))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world != args.gpus and not args.case:
+        raise SystemExit("bench.py: --gpus %d but WORLD_SIZE=%d" % (args.gpus, world))
     if args.case:
         run_case(args)
     elif args.impl == "reference":
