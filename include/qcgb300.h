@@ -298,15 +298,18 @@ int qc_qasm_write(int n, const qc_gate* gates, int ngates, char* buf, size_t cap
 /* ---- batches of circuits -----------------------------------------------------
  * Many independent circuits of different sizes and depths run in one
  * persistent kernel launch (optionally captured in a CUDA graph and replayed).
- * Each CTA takes circuits from an atomic work queue, largest first; a circuit
- * whose state fits in the CTA's shared memory (complex64 n <= 13, complex128
- * n <= 12) is simulated there from |0...0> and written to its state once;
- * larger ones are swept in global memory by a team of up to 16 CTAs (one per
- * 8 MB of state), which split every gate block and meet at a bounded barrier
- * between blocks; a barrier that gives up makes qc_batch_launch return
- * QC_ERR_TIMEOUT (results incomplete).  Fusion (greedy, k <= 4) is applied per
- * circuit; fuse_k < 0 lets the library time the candidates {1, 2, 3, 4} on the
- * batch once and keep the fastest. */
+ * A circuit whose state fits in a CTA's shared memory (complex64 n <= 13,
+ * complex128 n <= 12) is simulated there from |0...0> and written to its state
+ * once; larger ones are swept in global memory, by one CTA or by a team of up
+ * to 16 CTAs (one per 8 MB of state, or the tuned size), which split every
+ * gate block and meet at a bounded barrier between blocks; a barrier that
+ * gives up makes qc_batch_launch return QC_ERR_TIMEOUT (results incomplete).
+ * CTAs take work from two atomic queues: teams, largest work first, and
+ * single-CTA circuits, smallest first; a share of the CTAs proportional to the
+ * single-CTA work starts on the second queue, and a CTA whose queue is empty
+ * moves to the other.  Fusion (greedy, k <= 4) is applied per circuit;
+ * fuse_k < 0 lets the library time the candidates (k in {2, 3, 4}) x (4, 8 or
+ * 16 MB of state per team member) on the batch once and keep the fastest. */
 typedef struct {
   int n;                 /* qubits of the circuit (must equal its state's n) */
   int ngates;
@@ -423,6 +426,54 @@ int qc_adjoint_grad(int n, const qc_gate* gates, int ngates, const double* theta
 
 /* Number of parametric gates (RX/RY/RZ without controls) in a gate list. */
 int qc_count_params(const qc_gate* gates, int ngates, int* nparams);
+
+/* ---- one state over several shards ------------------------------------------
+ * A state of n qubits split over 2^g shards (one per rank or GPU): the g most
+ * significant qubits (qubits 0 .. g-1, Definition 1) are global -- rank r
+ * holds the 2^(n-g) amplitudes whose top g index bits equal r, global qubit p
+ * being bit g-1-p of r -- and each shard is an (n-g)-qubit state whose qubit j
+ * is qubit g + j of the register.  The paper simulates on one GPU; this
+ * layout extends Eq. (1)'s gate application to a register larger than one
+ * device's memory.
+ *
+ * qc_shard_plan (host only, no GPU needed): the steps that apply `gates` to
+ * the sharded state, in order.  QC_SHARD_GATE: apply `gate` (qubits numbered
+ * within a shard) on every rank r with (r & rank_mask) == rank_val -- its
+ * controls on global qubits became that condition.  QC_SHARD_EXCHANGE: every
+ * rank r trades the half of its shard whose bit `local_qubit` equals
+ * 1 - bit(r, rank_bit) with the same half of rank r ^ (1 << rank_bit) (the
+ * partner's half whose bit equals bit(r, rank_bit)), which swaps a global and
+ * a local qubit; a target on a global qubit is brought local this way first.
+ * Uncontrolled SWAP gates only relabel qubits and move no data.  The plan ends
+ * with the identity layout.  Gate records of QC_SHARD_GATE steps point at the
+ * caller's matrices.  steps == NULL: only *nsteps is written; otherwise
+ * QC_ERR_ARG when more than max_steps steps are needed (*nsteps says how many). */
+#define QC_SHARD_GATE 0
+#define QC_SHARD_EXCHANGE 1
+typedef struct {
+  int kind;            /* QC_SHARD_GATE or QC_SHARD_EXCHANGE */
+  qc_gate gate;        /* QC_SHARD_GATE: the gate in shard qubit numbering */
+  uint32_t rank_mask;  /* QC_SHARD_GATE: ranks r with (r & rank_mask) == rank_val apply it */
+  uint32_t rank_val;
+  int rank_bit;        /* QC_SHARD_EXCHANGE: partner rank = r ^ (1 << rank_bit) */
+  int local_qubit;     /* QC_SHARD_EXCHANGE: shard qubit whose halves are traded */
+} qc_shard_step;
+int qc_shard_plan(int n, int g, const qc_gate* gates, int ngates, qc_shard_step* steps, int max_steps,
+                  int* nsteps);
+
+/* One exchange between two shards held by this process: a's half with bit
+ * `local_qubit` = 1 - bit_a trades places with b's half with that bit = bit_a
+ * (bit_a = the rank bit of a; b is the partner).  Same n and dtype; b's memory
+ * must be accessible from a's device (the same device, or peer access enabled
+ * by the caller).  Enqueued on a's stream; in place, one pass over the halves. */
+int qc_shard_exchange(qc_state* a, qc_state* b, int local_qubit, int bit_a);
+
+/* Copy the half of s whose bit `local_qubit` equals `bit` into a contiguous
+ * device buffer of 2^(n-1) amplitudes (16-byte aligned), and back -- the two
+ * ends of an exchange between processes (the buffer travels by NCCL
+ * send/recv or any other transport).  Enqueued on s's stream. */
+int qc_shard_pack(const qc_state* s, int local_qubit, int bit, void* dev_buf);
+int qc_shard_unpack(qc_state* s, int local_qubit, int bit, const void* dev_buf);
 
 /* ---- diagnostics ---------------------------------------------------------- */
 /* Message of the last failing call on this thread ("" if none). */

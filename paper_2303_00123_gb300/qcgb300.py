@@ -67,6 +67,14 @@ class qc_grad_opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("arith", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
+class qc_shard_step(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("gate", qc_gate), ("rank_mask", ctypes.c_uint32),
+                ("rank_val", ctypes.c_uint32), ("rank_bit", ctypes.c_int), ("local_qubit", ctypes.c_int)]
+
+
+SHARD_GATE, SHARD_EXCHANGE = 0, 1
+
+
 class qc_pauli_sum(ctypes.Structure):
     _fields_ = [("nterms", ctypes.c_int), ("coeffs", ctypes.POINTER(ctypes.c_double)),
                 ("offsets", ctypes.POINTER(ctypes.c_int)), ("letters", ctypes.c_char_p),
@@ -119,6 +127,10 @@ def _load():
         "qc_batch_launch": [P, DP, DP],
         "qc_batch_info": [P, IP, IP, IP],
         "qc_batch_free": [P],
+        "qc_shard_plan": [I, I, ctypes.POINTER(qc_gate), I, ctypes.POINTER(qc_shard_step), I, IP],
+        "qc_shard_exchange": [P, P, I, I],
+        "qc_shard_pack": [P, I, I, P],
+        "qc_shard_unpack": [P, I, I, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -427,6 +439,51 @@ def fuse_plan(n: int, gates, fuse_k: int):
         out.append((tuple(b.qubits[:b.k]), tuple(b.controls[:b.nc]), tuple(b.cstates[:b.nc]), U.copy()))
     del keep
     return out
+
+
+def shard_plan(n: int, g: int, gates):
+    """Steps that apply `gates` to an n-qubit state split over 2^g shards
+    (qc_shard_plan).  Each step is ("gate", Gate, rank_mask, rank_val) -- the
+    gate in shard qubit numbering, applied on ranks r with r & mask == val --
+    or ("exchange", rank_bit, local_qubit)."""
+    from .circuits import Gate
+    arr, keep = gate_records(gates)
+    ns = ctypes.c_int(0)
+    _check(lib.qc_shard_plan(n, g, arr, len(gates), None, 0, ctypes.byref(ns)))
+    steps = (qc_shard_step * max(1, ns.value))()
+    _check(lib.qc_shard_plan(n, g, arr, len(gates), steps, ns.value, ctypes.byref(ns)))
+    out = []
+    for st in steps[:ns.value]:
+        if st.kind == SHARD_EXCHANGE:
+            out.append(("exchange", st.rank_bit, st.local_qubit))
+            continue
+        r = st.gate
+        qubits = tuple(r.qubits[:r.nq])
+        controls = tuple(r.controls[:r.nc])
+        cstates = tuple(r.cstates[:r.nc])
+        if r.kind == 0:
+            d = 1 << r.nq
+            m = np.array([complex(r.matrix[2 * j], r.matrix[2 * j + 1]) for j in range(d * d)]).reshape(d, d)
+            name = "U" if r.nq == 1 else ("U4" if r.nq == 2 else "UK")
+            gt = Gate(name, qubits, controls=controls, cstates=cstates, matrix=m)
+        else:
+            gt = Gate(_KIND_NAME[r.kind], qubits, controls=controls, cstates=cstates, theta=float(r.theta))
+        out.append(("gate", gt, st.rank_mask, st.rank_val))
+    del keep
+    return out
+
+
+def shard_exchange(a: "State", b: "State", local_qubit: int, bit_a: int):
+    """Trade a's half {bit(local_qubit) = 1 - bit_a} with b's half {= bit_a} (one kernel)."""
+    _check(lib.qc_shard_exchange(a.handle, b.handle, int(local_qubit), int(bit_a)))
+
+
+def shard_pack(s: "State", local_qubit: int, bit: int, dev_ptr: int):
+    _check(lib.qc_shard_pack(s.handle, int(local_qubit), int(bit), ctypes.c_void_p(dev_ptr)))
+
+
+def shard_unpack(s: "State", local_qubit: int, bit: int, dev_ptr: int):
+    _check(lib.qc_shard_unpack(s.handle, int(local_qubit), int(bit), ctypes.c_void_p(dev_ptr)))
 
 
 def device_status() -> dict:
