@@ -372,10 +372,12 @@ def run_gpu(args):
                 ev[3].record(stream)
         e2e_s = time.perf_counter() - t0
         torch.cuda.synchronize()
+        h2d_each = [round(e[0].elapsed_time(e[1]), 1) for e in evs]
         h2d = sum(e[0].elapsed_time(e[1]) for e in evs) / e2e_steps
         circ_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / e2e_steps
         d2h = sum(e[2].elapsed_time(e[3]) for e in evs) / e2e_steps
         wall = e2e_s / e2e_steps * 1e3
+        in_pinned = bool(host_in.is_pinned())
         del host_in, host_out, in_np, out_np
         bi = 2 * (1 << n) * elem
         e2e = {"value": gates_per_step * e2e_steps * world / e2e_s, "unit": "gates/s",
@@ -384,6 +386,7 @@ def run_gpu(args):
                    "wall": round(wall, 1), "h2d": round(h2d, 1), "circuits": round(circ_ms, 1), "d2h": round(d2h, 1),
                    "host_enqueue": round(enqueue_s / e2e_steps * 1e3, 1),
                    "other": round(wall - h2d - circ_ms - d2h, 1),
+                   "h2d_each_ms": h2d_each, "input_pinned": in_pinned,
                    "note": "h2d, circuits, d2h: CUDA events on the state's stream around each phase (two circuits "
                            "per step); host_enqueue: wall time of the apply calls (marshalling, planning, launches, "
                            "overlapping the device work); other = wall - h2d - circuits - d2h"}}
@@ -828,16 +831,26 @@ def extra_measurements(q, st, stream, brick, x, args):
                                 "complex128 and complex64, error vs the FP64 oracle at n=20; n=30 QFT (each H merged "
                                 "with its phase run, final SWAPs as one bit permutation); n=30 TFXY Trotter, 10 steps",
                     **fused}
-    # batched: 1024 circuits, one persistent launch vs one launch per gate
+    # batched: 1024 circuits, one persistent launch vs one launch per gate, and vs
+    # per-circuit fused launches spread over 8 streams
     specs = C.batch_specs(1024, seed=4)
     circs = [C.random_mix(n, d, seed=sd) for n, d, sd in specs]
     ngates = sum(len(g) for g in circs)
     sts = [q.State(n, q.C64) for n, _, _ in specs]
+    t0 = time.perf_counter()
     b = q.Batch(sts, circs, fuse_k=-1, use_graph=True, stream=stream)
+    tune_s = time.perf_counter() - t0
     b.launch(timing=True)
     comp, tot = b.launch(timing=True)
     info = b.info()
     b.free()
+    # algorithmic bytes: a shared-memory circuit writes its state once; a global
+    # one reads and writes it per launch op (the persistent plan's fused ops)
+    kk = info["fuse_k"]
+    abytes = 0.0
+    for (n_, _, _), g in zip(specs, circs):
+        sb = (1 << n_) * 8
+        abytes += sb if sb <= 64 * 1024 else 2 * sb * len(q.fuse_plan(n_, g, kk))
     for s2 in sts:
         s2.set_stream(stream)
     def one_by_one():
@@ -846,12 +859,34 @@ def extra_measurements(q, st, stream, brick, x, args):
             s2.apply_circuit(g)
     one_by_one()
     tb = _event_ms(stream, one_by_one)
+    streams = [torch.cuda.Stream() for _ in range(8)]
+    for i2, s2 in enumerate(sts):
+        s2.set_stream(streams[i2 % 8])
+    def fused_streams():
+        for s2, g in zip(sts, circs):
+            s2.set_basis(0)
+            s2.apply_circuit(g, fuse_k=kk)
+    fused_streams()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fused_streams()
+    torch.cuda.synchronize()
+    tf = (time.perf_counter() - t0) * 1e3
     for s2 in sts:
         s2.free()
+    peak, _ = measured_peaks()
     out["batched"] = {"workload": "1024 random circuits, n~U[10,24], depth~U[50,300], complex64",
                       "gates": ngates, "persistent_ms": round(tot, 1), "gates_per_s": round(ngates / tot * 1e3, 1),
                       "p50_ms": round(float(np.percentile(comp, 50)), 1), "p99_ms": round(float(np.percentile(comp, 99)), 1),
-                      "one_launch_per_gate_ms": round(tb, 1), "speedup": round(tb / tot, 2), "fuse_k": info["fuse_k"]}
+                      "p50_over_makespan": round(float(np.percentile(comp, 50)) / tot, 3),
+                      "roofline": {"bound": "hbm", "algorithmic_GB": round(abytes / 1e9, 2),
+                                   "achieved": round(abytes / (tot * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                                   "frac": round(abytes / (tot * 1e-3) / 1e9 / peak, 4),
+                                   "note": "shared-memory circuits: one state write; others: 2 N E per fused op; "
+                                           "states below ~100 MB may stay in L2, so the fraction can exceed HBM's"},
+                      "one_launch_per_gate_ms": round(tb, 1), "speedup": round(tb / tot, 2),
+                      "fused_launches_8_streams_ms": round(tf, 1), "speedup_vs_fused_streams": round(tf / tot, 2),
+                      "fuse_k": kk, "autotune_s": round(tune_s, 2)}
     # adjoint gradients vs parameter shift through the per-gate path (sampled, extrapolated)
     n, layers, B = 20, 10, 64
     th = C.hea_thetas(n, layers, seed=2025, batch=B)

@@ -2,11 +2,14 @@
 //
 // Host: every circuit is planned (resolved, optionally fused into blocks of
 // k <= 4 qubits) into ops {targets, controls, dense matrix}; all ops, matrices
-// and per-circuit records go to one device allocation.  Circuits are ordered by
-// work (2^n * ops), largest first.
+// and per-circuit records go to one device allocation.  Two queues: circuits
+// swept by teams, largest work (2^n * ops per member) first, and single-CTA
+// circuits, smallest work first.
 //
 // Device: a persistent kernel with as many CTAs as fit at once (all of them
-// co-resident).  A CTA takes the next entry from an atomic queue:
+// co-resident).  A share of the CTAs proportional to the single-CTA work
+// starts on that queue, the rest on the team queue; a CTA whose queue is empty
+// takes from the other.  A CTA takes the next entry:
 //   * shared-memory mode (state <= kSmemState bytes): one CTA builds the state
 //     as |0...0> in shared memory, applies every op there (threads over the
 //     op's groups, __syncthreads between ops) and writes the final state to
@@ -16,9 +19,10 @@
 //     op by op, each member taking 1/T of every op's groups, with a team
 //     barrier (a per-circuit arrival counter) between ops.
 // Deadlock freedom: the grid never exceeds the co-resident capacity, team
-// entries are consecutive and T <= 16 < grid, so at most one team is partly
-// dequeued at any time and its missing members are the next entries taken by
-// CTAs that finish work that waits on nothing unfinished.  Every barrier wait
+// entries are consecutive in their own queue and T <= 16 < grid, so at most
+// one team is partly dequeued at any time and its missing members are the next
+// team entries, taken by CTAs that finish work that waits on nothing
+// unfinished (single-CTA circuits never wait).  Every barrier wait
 // is bounded; a wait that gives up sets a status word (the host returns
 // QC_ERR_TIMEOUT) and the team abandons that circuit.
 // %globaltimer stamps give each circuit's completion time.
@@ -59,7 +63,8 @@ struct BEntry {
 };
 
 struct BCtl {
-  unsigned int queue;       // next entry
+  unsigned int queue;       // next entry of the team queue
+  unsigned int queue2;      // next entry of the single-CTA queue
   int status;               // 0, or 1 when a team barrier gave up
   int skip_circ;            // test hook: this circuit's member `skip_member` never arrives (-1: off)
   int skip_member;
@@ -134,8 +139,8 @@ __device__ bool team_barrier(unsigned int* bar, unsigned int target, bool arrive
 
 template <class Ar>
 __global__ void __launch_bounds__(kBT, 2)
-k_batch(const BCirc* __restrict__ circs, const BEntry* __restrict__ entries, int nentries, int ncirc,
-        const BOp* __restrict__ ops, const typename Ar::coef_t* __restrict__ coefs,
+k_batch(const BCirc* __restrict__ circs, const BEntry* __restrict__ entries, int nteam_entries, int nsingle,
+        int nsingle_ctas, int ncirc, const BOp* __restrict__ ops, const typename Ar::coef_t* __restrict__ coefs,
         BCtl* __restrict__ ctl, unsigned int* __restrict__ bars, unsigned long long* __restrict__ times) {
   using raw_t = typename Ar::raw_t;
   using coef_t = typename Ar::coef_t;
@@ -144,13 +149,31 @@ k_batch(const BCirc* __restrict__ circs, const BEntry* __restrict__ entries, int
   coef_t* sM = reinterpret_cast<coef_t*>(smem + kSmemState);
   uint64_t* smoff = reinterpret_cast<uint64_t*>(smem + kSmemState + kMaxD * kMaxD * sizeof(coef_t));
   __shared__ unsigned int s_next;
-  if (threadIdx.x == 0) atomicMin(&times[ncirc], gtimer());   // launch start (earliest CTA)
+  __shared__ int s_queue;            // the queue this CTA takes from now: 0 single-CTA, 1 team
+  if (threadIdx.x == 0) {
+    atomicMin(&times[ncirc], gtimer());   // launch start (earliest CTA)
+    s_queue = (int)blockIdx.x < nsingle_ctas ? 0 : 1;
+  }
   for (;;) {
-    if (threadIdx.x == 0) s_next = atomicAdd(&ctl->queue, 1u);
+    if (threadIdx.x == 0) {
+      // the home queue first, then the other one; done when both are empty
+      unsigned int e = 0xFFFFFFFFu;
+      for (int tries = 0; tries < 2 && e == 0xFFFFFFFFu; tries++) {
+        if (s_queue == 0) {
+          const unsigned int qv = atomicAdd(&ctl->queue2, 1u);
+          if (qv < (unsigned int)nsingle) e = (unsigned int)nteam_entries + qv;
+        } else {
+          const unsigned int qv = atomicAdd(&ctl->queue, 1u);
+          if (qv < (unsigned int)nteam_entries) e = qv;
+        }
+        if (e == 0xFFFFFFFFu) s_queue ^= 1;
+      }
+      s_next = e;
+    }
     __syncthreads();
     const unsigned int qi = s_next;
     __syncthreads();
-    if (qi >= (unsigned int)nentries) break;
+    if (qi == 0xFFFFFFFFu) break;
     const BEntry e = entries[qi];
     const BCirc c = circs[e.circ];
     const uint64_t N = 1ull << c.n;
@@ -215,7 +238,7 @@ k_batch(const BCirc* __restrict__ circs, const BEntry* __restrict__ entries, int
 struct qc_batch {
   int ncirc = 0;
   int dtype = QC_C64, arith = QC_ARITH_AUTO, device = 0;
-  int fuse_k = 0, nops = 0, nsmem = 0;
+  int fuse_k = 0, nops = 0, nsmem = 0, team_mb = 8;
   cudaStream_t stream = nullptr;
   void* dmem = nullptr;        // [circs][entries][ops][coefs][ctl][bars][times]
   BCirc* dcircs = nullptr;
@@ -224,6 +247,9 @@ struct qc_batch {
   BOp* dops = nullptr;
   void* dcoefs = nullptr;
   BCtl* dctl = nullptr;
+  int nteam_entries = 0;       // entries [0, nteam_entries): teams of 2..16 CTAs, largest work first
+  int nsingle = 0;             // entries after them: single-CTA circuits, smallest work first
+  int nsingle_ctas = 0;        // CTAs that start on the single-CTA queue
   unsigned int* dbars = nullptr;
   unsigned long long* dtimes = nullptr;
   BCtl hctl;
@@ -236,7 +262,8 @@ struct qc_batch {
 namespace {
 
 template <class Ar>
-int build_tables(qc_batch* b, qc_state* const* states, const qc_circuit_desc* circs, int ncirc, int fuse_k) {
+int build_tables(qc_batch* b, qc_state* const* states, const qc_circuit_desc* circs, int ncirc, int fuse_k,
+                 int team_mb) {
   using coef_t = typename Ar::coef_t;
   std::vector<BCirc> hc(ncirc);
   std::vector<BOp> hops;
@@ -269,25 +296,37 @@ int build_tables(qc_batch* b, qc_state* const* states, const qc_circuit_desc* ci
       for (int e = 0; e < D * D; e++) hcoef.push_back(Ar::make_coef(op.U[2 * e], op.U[2 * e + 1]));
       hops.push_back(bo);
     }
-    // team size: one CTA per 8 MB of state beyond shared memory, at most 16
+    // team size: one CTA per team_mb MB of state beyond shared memory, at most 16
     if (hc[i].smem) {
       hc[i].team = 1;
     } else {
       const size_t bytes = ((size_t)1 << d.n) * sizeof(typename Ar::raw_t);
       int T = 1;
-      while (T < 16 && bytes / (size_t)T > ((size_t)8 << 20)) T *= 2;
+      while (T < 16 && bytes / (size_t)T > ((size_t)team_mb << 20)) T *= 2;
       hc[i].team = T;
     }
     // work per member: sweeps over the state; shared-memory circuits cost a few times less per op
     work[i] = (double)((size_t)1 << d.n) * (double)(ops.size() + 1) * (hc[i].smem ? 0.25 : 1.0) / hc[i].team;
   }
-  // queue: largest work per member first; a team's entries are consecutive
+  // Two queues.  Teams (2..16 CTAs), largest work per member first, their
+  // entries consecutive (this order bounds the makespan); single-CTA circuits,
+  // smallest work first (early completions).  A share of the CTAs
+  // proportional to the single-CTA work starts on the second queue; a CTA
+  // whose queue is empty moves to the other one.
   std::vector<uint32_t> order(ncirc);
   std::iota(order.begin(), order.end(), 0u);
   std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) { return work[a] > work[c]; });
   std::vector<BEntry> ents;
+  double wteam = 0.0, wsingle = 0.0;
   for (uint32_t ci : order)
-    for (int m = 0; m < hc[ci].team; m++) ents.push_back(BEntry{ci, (uint32_t)m});
+    if (hc[ci].team > 1) {
+      for (int m = 0; m < hc[ci].team; m++) ents.push_back(BEntry{ci, (uint32_t)m});
+      wteam += work[ci] * hc[ci].team;
+    }
+  b->nteam_entries = (int)ents.size();
+  for (auto it = order.rbegin(); it != order.rend(); ++it)
+    if (hc[*it].team == 1) { ents.push_back(BEntry{*it, 0u}); wsingle += work[*it]; }
+  b->nsingle = (int)ents.size() - b->nteam_entries;
   const size_t sz_c = sizeof(BCirc) * ncirc, sz_e = (sizeof(BEntry) * ents.size() + 15) & ~(size_t)15;
   const size_t sz_op = sizeof(BOp) * std::max<size_t>(1, hops.size());
   const size_t sz_cf = (sizeof(coef_t) * std::max<size_t>(1, hcoef.size()) + 15) & ~(size_t)15;
@@ -324,6 +363,11 @@ int build_tables(qc_batch* b, qc_state* const* states, const qc_circuit_desc* ci
   // never more CTAs than can be resident at once: team barriers rely on it
   b->grid = std::max(1, std::min(b->nentries, qc_num_sms() * std::max(1, per_sm)));
   if (b->grid < 16 && b->nentries > b->grid) return qc_fail(QC_ERR_UNSUPPORTED, "device too small for batch teams");
+  // CTAs starting on the single-CTA queue: their share of the work, leaving at least 16 for the teams
+  int ns = (int)((double)b->grid * wsingle / std::max(1e-30, wteam + wsingle) + 0.5);
+  if (b->nsingle > 0) ns = std::max(ns, 1);
+  if (b->nteam_entries > 0) ns = std::min(ns, b->grid - 16);
+  b->nsingle_ctas = std::max(0, ns);
   return QC_OK;
 }
 
@@ -332,7 +376,8 @@ int enqueue(qc_batch* b) {
   QC_CUDA(cudaMemcpyAsync(b->dctl, &b->hctl, sizeof(BCtl), cudaMemcpyHostToDevice, b->stream));
   QC_CUDA(cudaMemsetAsync(b->dbars, 0, sizeof(unsigned int) * b->ncirc, b->stream));
   QC_CUDA(cudaMemsetAsync(b->dtimes + b->ncirc, 0xFF, sizeof(unsigned long long), b->stream));
-  k_batch<Ar><<<b->grid, kBT, b->smem, b->stream>>>(b->dcircs, b->dentries, b->nentries, b->ncirc, b->dops,
+  k_batch<Ar><<<b->grid, kBT, b->smem, b->stream>>>(b->dcircs, b->dentries, b->nteam_entries, b->nsingle,
+                                                   b->nsingle_ctas, b->ncirc, b->dops,
                                                    (const typename Ar::coef_t*)b->dcoefs, b->dctl, b->dbars,
                                                    b->dtimes);
   QC_LAUNCHED("k_batch");
@@ -352,10 +397,11 @@ int enqueue_any(qc_batch* b) {
   return enqueue<ArC128x>(b);
 }
 
-int build_any(qc_batch* b, qc_state* const* states, const qc_circuit_desc* circs, int ncirc, int fuse_k) {
-  if (b->dtype == QC_C64) return build_tables<ArC64>(b, states, circs, ncirc, fuse_k);
-  if (b->arith == QC_ARITH_NATIVE) return build_tables<ArC128>(b, states, circs, ncirc, fuse_k);
-  return build_tables<ArC128x>(b, states, circs, ncirc, fuse_k);
+int build_any(qc_batch* b, qc_state* const* states, const qc_circuit_desc* circs, int ncirc, int fuse_k,
+              int team_mb) {
+  if (b->dtype == QC_C64) return build_tables<ArC64>(b, states, circs, ncirc, fuse_k, team_mb);
+  if (b->arith == QC_ARITH_NATIVE) return build_tables<ArC128>(b, states, circs, ncirc, fuse_k, team_mb);
+  return build_tables<ArC128x>(b, states, circs, ncirc, fuse_k, team_mb);
 }
 
 int timed_run(qc_batch* b, float* ms) {
@@ -407,19 +453,25 @@ extern "C" int qc_batch_create(qc_state* const* states, const qc_circuit_desc* c
   b->hctl.spin_limit = o.spin_limit > 0 ? (unsigned long long)o.spin_limit : (1ull << 26);
   int rc = QC_OK;
   if (o.fuse_k < 0) {
-    // autotune: time the whole batch once per candidate width, keep the fastest
+    // autotune: time the whole batch once per candidate (fusion width, state
+    // bytes per team member), keep the fastest
     float best = 1e30f;
-    int bestk = 1;
-    for (int k : {1, 2, 3, 4}) {
-      rc = build_any(b, states, circs, ncirc, k);
-      float ms = 0.f;
-      if (rc == QC_OK) rc = timed_run(b, &ms);
+    int bestk = 1, bestmb = 8;
+    for (int k : {2, 3, 4}) {
+      for (int mb : {4, 8, 16}) {
+        rc = build_any(b, states, circs, ncirc, k, mb);
+        float ms = 0.f;
+        if (rc == QC_OK) rc = timed_run(b, &ms);
+        if (rc != QC_OK) break;
+        if (ms < best) { best = ms; bestk = k; bestmb = mb; }
+      }
       if (rc != QC_OK) break;
-      if (ms < best) { best = ms; bestk = k; }
     }
-    if (rc == QC_OK) rc = build_any(b, states, circs, ncirc, bestk);
+    b->team_mb = bestmb;
+    if (rc == QC_OK) rc = build_any(b, states, circs, ncirc, bestk, bestmb);
   } else {
-    rc = build_any(b, states, circs, ncirc, o.fuse_k);
+    b->team_mb = 8;
+    rc = build_any(b, states, circs, ncirc, o.fuse_k, 8);
   }
   if (rc == QC_OK && o.use_graph) {
     if (!b->stream) rc = qc_fail(QC_ERR_ARG, "graph capture needs a non-default stream");
