@@ -106,12 +106,17 @@ int qc_set_stream(qc_state* s, void* cuda_stream);
 int qc_set_arith(qc_state* s, int arith);
 
 /* Dense blocks on k = 3..5 qubits (fused gates, qc_apply_kq) run on the
- * tensor cores when enable != 0 (the default), else on the CUDA cores:
+ * tensor cores when enable != 0 (the default, 1), else on the CUDA cores:
  * complex64 with split-TF32 products (hi*hi + hi*lo + lo*hi, FP32
  * accumulators); complex128 under QC_ARITH_F32X2 with exact fp16 digit slices
  * (entries rounded to 48 bits against their group's largest exponent, six
  * base-2^8 digits; the matrix in seven; exact integer level sums; error about
- * 2^-47 of each 128-group's largest amplitude). */
+ * 2^-47 of each 128-group's largest amplitude).  enable = 2: complex128
+ * blocks whose tile holds exactly its groups (no control below the tile's run
+ * length) have their tiles staged by the Tensor Memory Accelerator instead of
+ * per-thread loads -- the same arithmetic and bit-identical results, measured
+ * slower (the staging buffer's traffic competes with the MMAs' operand reads
+ * for shared-memory bandwidth), so 1, per-thread loads, is the default. */
 int qc_set_fused_tc(qc_state* s, int enable);
 
 /* complex128 float-float dense and phase sweeps use packed FP32-pair
@@ -355,20 +360,26 @@ typedef struct {
 
 /* *out = <psi| H |psi> (real part), copied to the host (synchronises the
  * state's stream); the state is not modified.  The terms are evaluated in
- * passes over tiles of the state (see qc_expect_passes).  complex128: products
- * and sums in float-float arithmetic (47-bit amplitudes, exact hi*hi
- * products), block sums in FP64 -- about 1e-15 from the exact value for O(1)
- * coefficients.  complex64: FP32 products and per-thread partial sums of at
- * most 16 products, float-float across tiles, FP64 block sums -- within
- * about 1e-6 * sum |c_t|.  Deterministic (fixed grid, fixed reduction order). */
+ * passes over tiles of the state (see qc_expect_passes).  complex128:
+ * amplitudes split into float pairs (47 bits), products exact in their
+ * hi*hi part, each thread's sum of a term's products over its share of a
+ * tile accumulated without rounding error in a fixed-exponent chain (the
+ * rounding remainders and hi*lo cross terms in a second word), float-float
+ * across a tile's terms, FP64 across tiles -- about 1e-15 from the exact value
+ * for O(1) coefficients.  complex64: FP32 products and per-thread partial sums
+ * of at most 16 products, float-float across tiles, FP64 block sums -- within
+ * about 1e-6 * sum |c_t|.  QC_ERR_TIMEOUT as described at qc_device_status.
+ * Deterministic (fixed grid, fixed reduction order). */
 int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out);
 
 /* Host only: the number of passes qc_expect makes over an n-qubit state of
  * the given dtype for H.  A pass reads the state once, a tile of 2^12
- * (complex128) or 2^13 (complex64) amplitudes at a time, and evaluates every
- * term whose X/Y qubits fall in the span of the tile's bits; the tiles' bits
- * are chosen per pass so that few passes cover all terms.  Validates H like
- * qc_expect (QC_ERR_ARG on a malformed sum); an empty sum needs 0 passes. */
+ * amplitudes at a time (n >= 12: 3 low index bits and 9 generator masks;
+ * smaller states: one tile), and evaluates every term whose X/Y qubits fall
+ * in the span of the tile's bits; the tiles' bits are chosen per pass so
+ * that few passes cover all terms (a nearest-neighbour chain of n qubits:
+ * ceil((n - 3) / 9)).  Validates H like qc_expect (QC_ERR_ARG on a malformed
+ * sum); an empty sum needs 0 passes. */
 int qc_expect_passes(int n, int dtype, const qc_pauli_sum* H, int* npasses);
 
 /* <psi| H |psi> like qc_expect, for callers that cannot allocate device memory

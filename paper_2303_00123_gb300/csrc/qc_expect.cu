@@ -163,7 +163,7 @@ int get_scratch(int device, size_t bytes, void** p) {
 namespace {
 
 constexpr int kTileThreads = 256;
-constexpr int kTileMaxH = 8;       // generator masks per pass
+constexpr int kTileMaxH = 9;       // generator masks per pass
 constexpr int kGroupTerms = 2;     // pair terms evaluated together per flip mask
 
 struct TTerm {                     // one term inside a pass
@@ -187,6 +187,9 @@ struct TPass {                     // kernel parameter: one pass
   int ngroups, dt0, dnt;           // pair groups; diagonal terms [dt0, dt0 + dnt)
   int piv[kTileMaxH];              // pivot bit of generator i, ascending in i
   uint64_t gen[kTileMaxH];         // generator masks
+  int garr[4];                     // register-resident kernel: groups [garr[a], garr[a+1]) (a < 3;
+                                   // garr[3] .. ngroups: from shared memory) use arrangement a
+  int reg;                         // 1: k_pauli_reg (tiles of 2^12), 0: k_pauli_tile
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -251,6 +254,24 @@ template <> struct TileT<false> {
   }
 };
 
+// Swizzled tile layout of the register-resident kernel (below): local
+// amplitude l lives in the 16-byte chunk c ^ ((l >> 4) & 7), c = l for
+// complex128 (one amplitude per chunk) and c = l >> 1 for complex64 (two).
+template <bool C128>
+__device__ __forceinline__ uint32_t rslot(uint32_t l) { return (C128 ? l : (l >> 1)) ^ ((l >> 4) & 7u); }
+
+template <bool C128, bool SWZ>
+__device__ __forceinline__ typename TileT<C128>::amp tile_get(const unsigned char* t, uint32_t l) {
+  if constexpr (!SWZ) {
+    return TileT<C128>::get(t, l);
+  } else if constexpr (C128) {
+    const uint4 v = *(const uint4*)(t + (size_t)rslot<true>(l) * 16);
+    return {(uint64_t)v.x | ((uint64_t)v.y << 32), (uint64_t)v.z | ((uint64_t)v.w << 32)};
+  } else {
+    return {*(const uint64_t*)(t + (size_t)rslot<false>(l) * 16 + (l & 1u) * 8), 0ull};
+  }
+}
+
 // Load the tile with base index `base` into shared memory: 16-byte
 // asynchronous copies (cp.async, no registers held while they are in flight),
 // then each thread splits the complex128 entries it copied into hi + lo
@@ -288,7 +309,7 @@ __device__ __forceinline__ void load_tile(const unsigned char* __restrict__ psi,
 // local phase masks are nonzero (at most kGroupTerms terms, one accumulator
 // each); otherwise every term of the group has the same in-tile sum and one
 // accumulator serves them all (any number of terms).
-template <bool C128, bool IM, bool SIGNED>
+template <bool C128, bool IM, bool SIGNED, bool SWZ = false>
 __device__ __forceinline__ void tile_group(const unsigned char* tile, const TPass& P, const TGroup& g,
                                            uint64_t base, uint64_t zz, float& th, float& tl) {
   using T = TileT<C128>;
@@ -312,8 +333,8 @@ __device__ __forceinline__ void tile_group(const unsigned char* tile, const TPas
       uint32_t j = j0 + u * kTileThreads;
       if (!full) j = min(j, npairs - 1u);
       l[u] = j + (j & hm);
-      a[u] = T::get(tile, l[u]);
-      b[u] = T::get(tile, l[u] ^ g.fl);
+      a[u] = tile_get<C128, SWZ>(tile, l[u]);
+      b[u] = tile_get<C128, SWZ>(tile, l[u] ^ g.fl);
     }
 #pragma unroll
     for (int u = 0; u < UNR; u++) {
@@ -528,6 +549,355 @@ k_pauli_tile(const unsigned char* __restrict__ psi, const __grid_constant__ TPas
   if (threadIdx.x == 0) partial[blockIdx.x] = bs;
 }
 
+// ---- register-resident passes ---------------------------------------------
+// Tiles of 2^12 amplitudes, 256 threads.  Each thread holds 16 amplitudes of
+// the tile in registers: those whose local index differs only in four
+// "register bits".  Three arrangements put the local bits [0, 4), [4, 8) and
+// [8, 12) in registers in turn; the tile passes through shared memory between
+// them in a swizzled layout (rslot) that keeps every one of these accesses
+// free of bank conflicts.  A pair term whose local flip mask FL lies within
+// the register bits of an arrangement pairs amplitudes held by one thread, so
+// the term costs no shared-memory traffic at all; other pair terms read the
+// tile from shared memory as in k_pauli_tile.  Diagonal terms use the
+// Walsh-Hadamard transform of the 16 |psi|^2 of arrangement 0.
+//
+// complex128 pair sums run in a fixed-binade chain instead of float-float
+// TwoSum steps: with sigma = 1.5 * 2^E and 2^E at least four times the largest
+// possible partial sum, t = fma(b, a, t) stays in [2^E, 2^(E+1)), so t - t'
+// is exact (Sterbenz) and the product's remainder fma(b, a, t - t') is the
+// rounding error of the step (exact up to 2^-24 of itself); the remainders and
+// the hi*lo cross terms add up in a second word.  Three instructions per
+// product instead of eight; the in-tile sum is (t - sigma) + lo.
+constexpr int kRegL = 12;
+
+__device__ __forceinline__ uint32_t sgn_bits(uint32_t odd) { return (odd & 1u) << 31; }
+
+// sigma (packed twice) for 8 products of amplitudes whose components are at most mx
+__device__ __forceinline__ uint64_t chain_sigma(float mx) {
+  const int ef = (int)((__float_as_uint(mx) >> 23) & 0xFFu);
+  int e = 2 * ef - 120;                  // 2^(e-127) >= 32 mx^2
+  e = e < 24 ? 24 : (e > 254 ? 254 : e);
+  const uint32_t sg = ((uint32_t)e << 23) | 0x00400000u;
+  return (uint64_t)sg | ((uint64_t)sg << 32);
+}
+
+// One group of pair terms over the 16 register amplitudes (register bits of
+// the current arrangement, the group's flip mask FLR in them).  lsign[k]: the
+// parity of the thread's fixed local bits & QL of term k; qlr[k]: QL restricted
+// to the register bits.  Results go to (vh, vl) per accumulator.
+template <bool C128, int FLR, bool IM, bool SIGNED>
+__device__ __forceinline__ void reg_pairs(const uint64_t* ah, const uint64_t* al, uint64_t sig, const uint32_t* lsign,
+                                          const uint32_t* qlr, int nt, float* vh, float* vl) {
+  constexpr int NA = SIGNED ? kGroupTerms : 1;
+  constexpr int PIV = FLR >= 8 ? 8 : (FLR >= 4 ? 4 : (FLR >= 2 ? 2 : 1));
+  // two independent chains per accumulator (alternate pairs): twice the
+  // instruction-level parallelism of one serial chain
+  uint64_t t[2][NA], lo[2][NA];
+#pragma unroll
+  for (int c = 0; c < 2; c++)
+#pragma unroll
+    for (int k = 0; k < NA; k++) { t[c][k] = C128 ? sig : 0ull; lo[c][k] = 0ull; }
+  int npair = 0;
+#pragma unroll
+  for (int r = 0; r < 16; r++) {
+    if (r & PIV) continue;
+    const int ch = (npair++) & 1;          // compile-time after unrolling
+    const int p = r ^ FLR;                 // partner: conj(psi_{y ^ F}) psi_y
+    const uint64_t ahp = IM ? P2::swp(ah[r]) : ah[r];
+#pragma unroll
+    for (int k = 0; k < NA; k++) {
+      if (SIGNED && k >= nt) break;
+      uint64_t bh = ah[p];
+      if constexpr (SIGNED) {
+        const uint32_t sb = sgn_bits(lsign[k] ^ (uint32_t)__popc((uint32_t)r & qlr[k]));
+        bh ^= (uint64_t)sb | ((uint64_t)sb << 32);
+      }
+      if constexpr (C128) {
+        const uint64_t alp = IM ? P2::swp(al[r]) : al[r];
+        uint64_t bl = al[p];
+        if constexpr (SIGNED) {
+          const uint32_t sb = sgn_bits(lsign[k] ^ (uint32_t)__popc((uint32_t)r & qlr[k]));
+          bl ^= (uint64_t)sb | ((uint64_t)sb << 32);
+        }
+        const uint64_t t1 = P2::fma2(bh, ahp, t[ch][k]);
+        const uint64_t rr = P2::fma2(bh, ahp, P2::sub2(t[ch][k], t1));
+        t[ch][k] = t1;
+        lo[ch][k] = P2::fma2(bl, ahp, P2::fma2(bh, alp, P2::add2(lo[ch][k], rr)));
+      } else {
+        t[ch][k] = P2::fma2(bh, ahp, t[ch][k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NA; k++) {
+    // (t0 - sigma) + (t1 - sigma): multiples of ulp(sigma) below 2^(E-2) each, so exact
+    const uint64_t hi = C128 ? P2::add2(P2::sub2(t[0][k], sig), P2::sub2(t[1][k], sig)) : P2::add2(t[0][k], t[1][k]);
+    const uint64_t lok = P2::add2(lo[0][k], lo[1][k]);
+    const float hx = P2::lo32(hi), lx = P2::lo32(lok);
+    const float hy = IM ? -P2::hi32(hi) : P2::hi32(hi);
+    const float ly = IM ? -P2::hi32(lok) : P2::hi32(lok);
+    float ve;
+    two_sum(hx, hy, vh[k], ve);
+    vl[k] = __fadd_rn(ve, __fadd_rn(lx, ly));
+  }
+}
+
+template <bool C128, int FLR>
+__device__ __forceinline__ void reg_pairs_kind(uint32_t kind, const uint64_t* ah, const uint64_t* al, uint64_t sig,
+                                               const uint32_t* lsign, const uint32_t* qlr, int nt, float* vh,
+                                               float* vl) {
+  switch (kind) {
+    case 0: reg_pairs<C128, FLR, false, false>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
+    case 1: reg_pairs<C128, FLR, true, false>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
+    case 2: reg_pairs<C128, FLR, false, true>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
+    default: reg_pairs<C128, FLR, true, true>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
+  }
+}
+
+// The groups [g0, g1) of arrangement `a` (register bits [4a, 4a + 4)) for this
+// thread's registers; lbase = the thread's local index with zero register bits.
+template <bool C128>
+__device__ __forceinline__ void reg_groups(const TPass& P, int g0, int g1, int a, uint32_t lbase, uint64_t base,
+                                           const uint64_t* ah, const uint64_t* al, uint64_t sig, float& th,
+                                           float& tl) {
+  for (int gi = g0; gi < g1; gi++) {
+    const uint32_t fl = __ldg(&P.groups[gi].fl);
+    const int t0 = __ldg(&P.groups[gi].t0);
+    const int nt = __ldg(&P.groups[gi].nt);
+    const uint32_t kind = __ldg(&P.groups[gi].kind);
+    static_assert(kGroupTerms == 2, "two accumulators per signed group");
+    uint32_t lsign[kGroupTerms] = {0u, 0u}, qlr[kGroupTerms] = {0u, 0u};
+    if (kind & 2u) {
+      const uint32_t q0 = __ldg(&P.terms[t0].ql);
+      lsign[0] = (uint32_t)__popc(lbase & q0) & 1u;
+      qlr[0] = (q0 >> (4 * a)) & 15u;
+      if (nt > 1) {
+        const uint32_t q1 = __ldg(&P.terms[t0 + 1].ql);
+        lsign[1] = (uint32_t)__popc(lbase & q1) & 1u;
+        qlr[1] = (q1 >> (4 * a)) & 15u;
+      }
+    }
+    float vh[kGroupTerms] = {0.f, 0.f}, vl[kGroupTerms] = {0.f, 0.f};
+    switch ((fl >> (4 * a)) & 15u) {
+#define QC_REG_CASE(F) case F: reg_pairs_kind<C128, F>(kind, ah, al, sig, lsign, qlr, nt, vh, vl); break;
+      QC_REG_CASE(1) QC_REG_CASE(2) QC_REG_CASE(3) QC_REG_CASE(4) QC_REG_CASE(5) QC_REG_CASE(6) QC_REG_CASE(7)
+      QC_REG_CASE(8) QC_REG_CASE(9) QC_REG_CASE(10) QC_REG_CASE(11) QC_REG_CASE(12) QC_REG_CASE(13)
+      QC_REG_CASE(14) QC_REG_CASE(15)
+#undef QC_REG_CASE
+      default: break;
+    }
+    const bool signed_ = (kind & 2u) != 0;
+    for (int k = 0; k < nt; k++) {
+      const TTerm* tt = &P.terms[t0 + k];
+      const float xh = (signed_ && k == 1) ? vh[1] : vh[0];
+      const float xl = (signed_ && k == 1) ? vl[1] : vl[0];
+      const bool neg = __popcll(base & __ldg(&tt->q)) & 1;
+      acc_scaled(th, tl, __ldg(&tt->kh), __ldg(&tt->kl), neg ? -xh : xh, neg ? -xl : xl);
+    }
+  }
+}
+
+// Load the 16 register amplitudes of arrangement a (complex128: the split form
+// (hi pair, lo pair) from shared memory; RAW: the raw doubles, split here).
+template <bool C128, bool RAW>
+__device__ __forceinline__ void reg_load(const unsigned char* tile, int a, uint32_t lbase, uint64_t* ah, uint64_t* al) {
+  if (!C128 && a == 0) {
+    // complex64, register bits [0, 4): the thread's 8 chunks, 16 bytes each
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t l = lbase | (uint32_t)(2 * k);
+      const uint4 v = *(const uint4*)(tile + (size_t)rslot<false>(l) * 16);
+      ah[2 * k] = (uint64_t)v.x | ((uint64_t)v.y << 32);
+      ah[2 * k + 1] = (uint64_t)v.z | ((uint64_t)v.w << 32);
+      al[2 * k] = al[2 * k + 1] = 0ull;
+    }
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < 16; r++) {
+    const uint32_t l = lbase | ((uint32_t)r << (4 * a));
+    if constexpr (C128) {
+      const uint4 v = *(const uint4*)(tile + (size_t)rslot<true>(l) * 16);
+      if constexpr (RAW) {
+        const ArC128x::ff re = ArC128x::split(v.x, v.y);
+        const ArC128x::ff im = ArC128x::split(v.z, v.w);
+        ah[r] = P2::pk(re.h, im.h);
+        al[r] = P2::pk(re.l, im.l);
+      } else {
+        ah[r] = (uint64_t)v.x | ((uint64_t)v.y << 32);
+        al[r] = (uint64_t)v.z | ((uint64_t)v.w << 32);
+      }
+    } else {
+      ah[r] = *(const uint64_t*)(tile + (size_t)rslot<false>(l) * 16 + (l & 1u) * 8);
+      al[r] = 0ull;
+    }
+  }
+}
+
+// largest |component| (hi parts) of the 16 register amplitudes
+__device__ __forceinline__ float reg_max(const uint64_t* ah) {
+  float m = 0.f;
+#pragma unroll
+  for (int r = 0; r < 16; r++) m = fmaxf(m, fmaxf(fabsf(P2::lo32(ah[r])), fabsf(P2::hi32(ah[r]))));
+  return m;
+}
+
+template <bool C128>
+__global__ void __launch_bounds__(kTileThreads, C128 ? 2 : 4)
+k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass P, double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  constexpr uint32_t kChunks = C128 ? (1u << kRegL) : (1u << (kRegL - 1));   // 16-byte chunks per tile
+  unsigned char* tile = rsm;
+  uint64_t* gtab = (uint64_t*)(rsm + (size_t)kChunks * 16);
+  for (int c = threadIdx.x; c < (1 << P.h); c += kTileThreads) {
+    uint64_t g = 0;
+    for (int i = 0; i < P.h; i++)
+      if ((c >> i) & 1) g ^= P.gen[i];
+    gtab[c] = g;
+  }
+  const uint64_t zz = P.ntiles >> 63;
+  const uint32_t t = threadIdx.x;
+  const uint32_t lowm = (1u << P.m) - 1u;
+  const uint32_t lb0 = t << 4;                                   // arrangement 0: bits [0, 4) in registers
+  const uint32_t lb1 = (t & 15u) | ((t >> 4) << 8);              // arrangement 1: bits [4, 8)
+  const uint32_t lb2 = t & 255u;                                 // arrangement 2: bits [8, 12)
+  double tot = 0.0;
+  for (uint64_t tix = blockIdx.x; tix < P.ntiles; tix += gridDim.x) {
+    float th = 0.f, tl = 0.f;
+    uint64_t base = tix << P.m;
+    for (int i = 0; i < P.h; i++) base = qc_insert_zero(base, P.piv[i]);
+    __syncthreads();                 // previous tile consumed, gtab written
+    {
+      // raw amplitudes, 16-byte cp.async chunks into their swizzled slots
+      constexpr uint32_t CA = C128 ? 1u : 2u;                   // amplitudes per chunk
+      const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile);
+      for (uint32_t v = t; v < kChunks; v += kTileThreads) {
+        const uint32_t l = v * CA;
+        const uint64_t y = (base ^ gtab[l >> P.m]) + (l & lowm);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                     :: "r"(sbase + rslot<C128>(l) * 16u), "l"(psi + y * (C128 ? 16 : 8)) : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    uint64_t ah[16], al[16];
+    // arrangement 0: raw -> split in registers, pair groups, diagonal terms, split form back
+    reg_load<C128, true>(tile, 0, lb0, ah, al);
+    if (P.garr[1] > P.garr[0])
+      reg_groups<C128>(P, P.garr[0], P.garr[1], 0, lb0, base, ah, al, chain_sigma(reg_max(ah)), th, tl);
+    unsigned char* own = tile + (size_t)(C128 ? lb0 : (lb0 >> 1)) * 16;   // this thread's 16 amplitudes' chunks
+    if (P.dnt > 0) {
+      // |psi|^2 of the 16 amplitudes, Walsh-Hadamard transform over the register bits
+      float ph[16], pl[16];
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const uint64_t p = prod2(ah[k], ah[k], zz);
+        if constexpr (C128) {
+          uint64_t e = P2::fma2(ah[k], ah[k], neg2(p));
+          e = P2::add2(e, P2::mul2(P2::add2(ah[k], ah[k]), al[k]));
+          float s2, r2;
+          two_sum(P2::lo32(p), P2::hi32(p), s2, r2);
+          ph[k] = s2;
+          pl[k] = __fadd_rn(r2, __fadd_rn(P2::lo32(e), P2::hi32(e)));
+        } else {
+          ph[k] = __fadd_rn(P2::lo32(p), P2::hi32(p));
+          pl[k] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int b = 1; b < 16; b <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+          if (!(k & b)) {
+            const float xh = ph[k], xl = pl[k], yh = ph[k | b], yl = pl[k | b];
+            if constexpr (C128) {
+              float s2, e2;
+              two_sum(xh, yh, s2, e2);
+              ph[k] = s2;
+              pl[k] = __fadd_rn(__fadd_rn(xl, yl), e2);
+              two_sum(xh, -yh, s2, e2);
+              ph[k | b] = s2;
+              pl[k | b] = __fadd_rn(__fsub_rn(xl, yl), e2);
+            } else {
+              ph[k] = __fadd_rn(xh, yh);
+              ph[k | b] = __fsub_rn(xh, yh);
+            }
+          }
+        }
+      }
+      // W[u] into this thread's own chunks, entry u at 8 (u ^ (lane & 15)) bytes:
+      // the 16 lanes of a wavefront use 16 different bank pairs
+      const uint32_t wsw = t & 15u;
+#pragma unroll
+      for (int k = 0; k < 16; k++) *(float2*)(own + 8 * ((uint32_t)k ^ wsw)) = make_float2(ph[k], pl[k]);
+      const uint64_t y0 = base ^ gtab[lb0 >> P.m] ^ (lb0 & lowm);
+      float dsum = 0.f;
+      for (int ti = P.dt0; ti < P.dt0 + P.dnt; ti++) {
+        const TTerm* tt = &P.terms[ti];
+        const uint32_t u = __ldg(&tt->ql) & 15u;
+        const float2 w = *(const float2*)(own + 8 * (u ^ wsw));
+        const uint32_t sb = (uint32_t)__popcll(y0 & __ldg(&tt->q)) << 31;
+        if constexpr (C128)
+          acc_scaled(th, tl, __uint_as_float(__float_as_uint(__ldg(&tt->kh)) ^ sb),
+                     __uint_as_float(__float_as_uint(__ldg(&tt->kl)) ^ sb), w.x, w.y);
+        else
+          dsum = __fmaf_rn(__uint_as_float(__float_as_uint(__ldg(&tt->kh)) ^ sb), w.x, dsum);
+      }
+      if constexpr (!C128) {
+        float s2, e2;
+        two_sum(th, dsum, s2, e2);
+        th = s2;
+        tl = __fadd_rn(tl, e2);
+      }
+    }
+    const bool later = P.garr[3] > P.garr[1] || P.ngroups > P.garr[3];
+    if (later && (C128 || P.dnt > 0)) {
+      // the split form (complex128) or the amplitudes themselves (complex64) back into the own chunks
+      if constexpr (C128) {
+#pragma unroll
+        for (int r = 0; r < 16; r++)
+          *(uint4*)(tile + (size_t)rslot<true>(lb0 | (uint32_t)r) * 16) =
+              make_uint4((uint32_t)ah[r], (uint32_t)(ah[r] >> 32), (uint32_t)al[r], (uint32_t)(al[r] >> 32));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+          *(uint4*)(tile + (size_t)rslot<false>(lb0 | (uint32_t)(2 * k)) * 16) =
+              make_uint4((uint32_t)ah[2 * k], (uint32_t)(ah[2 * k] >> 32), (uint32_t)ah[2 * k + 1],
+                         (uint32_t)(ah[2 * k + 1] >> 32));
+      }
+    }
+    if (later) {
+      __syncthreads();
+      if (P.garr[2] > P.garr[1]) {
+        reg_load<C128, false>(tile, 1, lb1, ah, al);
+        reg_groups<C128>(P, P.garr[1], P.garr[2], 1, lb1, base, ah, al, chain_sigma(reg_max(ah)), th, tl);
+      }
+      if (P.garr[3] > P.garr[2]) {
+        reg_load<C128, false>(tile, 2, lb2, ah, al);
+        reg_groups<C128>(P, P.garr[2], P.garr[3], 2, lb2, base, ah, al, chain_sigma(reg_max(ah)), th, tl);
+      }
+      for (int gi = P.garr[3]; gi < P.ngroups; gi++) {
+        TGroup g;
+        g.fl = __ldg(&P.groups[gi].fl);
+        g.pivot = __ldg(&P.groups[gi].pivot);
+        g.t0 = __ldg(&P.groups[gi].t0);
+        g.nt = __ldg(&P.groups[gi].nt);
+        g.kind = __ldg(&P.groups[gi].kind);
+        switch (g.kind) {
+          case 0: tile_group<C128, false, false, true>(tile, P, g, base, zz, th, tl); break;
+          case 1: tile_group<C128, true, false, true>(tile, P, g, base, zz, th, tl); break;
+          case 2: tile_group<C128, false, true, true>(tile, P, g, base, zz, th, tl); break;
+          default: tile_group<C128, true, true, true>(tile, P, g, base, zz, th, tl); break;
+        }
+      }
+    }
+    tot += ArC128x::f2d(th) + ArC128x::f2d(tl);
+  }
+  const double bs = block_sum(tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+}
+
 // ---- host planning --------------------------------------------------------
 struct HTerm { uint64_t F, Q; int ny; double c; };
 
@@ -614,7 +984,12 @@ int tile_plan(int n, bool c128, const std::vector<HTerm>& terms_in, TilePlan& pl
       }
     }
   }
-  const int Lmax = c128 ? 12 : 13, mdef = c128 ? 5 : 6;
+  // n >= 12: the register-resident kernel, tiles of 2^12 amplitudes with 3 low
+  // bits (runs of 8 amplitudes, 64 or 128 contiguous bytes) and 9 generators --
+  // 3 passes for a nearest-neighbour chain of 30 qubits instead of 4 with 5
+  // low bits and 7 generators
+  const bool reg = n >= kRegL;
+  const int Lmax = reg ? kRegL : (c128 ? 12 : 13), mdef = reg ? 3 : (c128 ? 5 : 6);
   const int L = std::min(n, Lmax);
   const int m = std::min(mdef, L);
   const int h = L - m;
@@ -679,6 +1054,7 @@ int tile_plan(int n, bool c128, const std::vector<HTerm>& terms_in, TilePlan& pl
     P.h = h;
     P.L = L;
     P.wb = L >= 8 ? 4 : 0;
+    P.reg = reg ? 1 : 0;
     for (int i = 0; i < h; i++) {
       P.gen[i] = p.basis.v[i];
       P.piv[i] = 63 - __builtin_clzll(p.basis.v[i]);
@@ -723,18 +1099,31 @@ int tile_plan(int n, bool c128, const std::vector<HTerm>& terms_in, TilePlan& pl
       for (size_t k = 0; k < cnt; k++) push_term(v[i0 + k], true);
       plan.groups.push_back(g);
     };
-    for (auto& kv : by_fl) {
-      // split by Re / Im weight and by whether the phase mask reaches into the tile
-      std::vector<const HTerm*> part[4];
-      for (const HTerm* t : kv.second) part[(t->ny & 1) | (local_q(t->Q) ? 2 : 0)].push_back(t);
-      for (uint32_t kind = 0; kind < 4; kind++) {
-        const std::vector<const HTerm*>& v = part[kind];
-        if (v.empty()) continue;
-        if (kind & 2u) {
-          for (size_t i = 0; i < v.size(); i += kGroupTerms)
-            push_group(kv.first, kind, v, i, std::min<size_t>(kGroupTerms, v.size() - i));
-        } else {
-          push_group(kv.first, kind, v, 0, v.size());
+    // register-resident kernel: groups whose local flip mask lies in the local
+    // bits [4a, 4a + 4) come first, arrangement a = 0, 1, 2; the rest read the
+    // tile from shared memory
+    auto arrangement = [&](uint32_t fl) {
+      if (!reg) return 3;
+      for (int a = 0; a < 3; a++)
+        if ((fl & ~(15u << (4 * a))) == 0) return a;
+      return 3;
+    };
+    for (int a = 0; a < 4; a++) {
+      P.garr[a] = (int)plan.groups.size() - g_begin;
+      for (auto& kv : by_fl) {
+        if (arrangement(kv.first) != a) continue;
+        // split by Re / Im weight and by whether the phase mask reaches into the tile
+        std::vector<const HTerm*> part[4];
+        for (const HTerm* t : kv.second) part[(t->ny & 1) | (local_q(t->Q) ? 2 : 0)].push_back(t);
+        for (uint32_t kind = 0; kind < 4; kind++) {
+          const std::vector<const HTerm*>& v = part[kind];
+          if (v.empty()) continue;
+          if (kind & 2u) {
+            for (size_t i = 0; i < v.size(); i += kGroupTerms)
+              push_group(kv.first, kind, v, i, std::min<size_t>(kGroupTerms, v.size() - i));
+          } else {
+            push_group(kv.first, kind, v, 0, v.size());
+          }
         }
       }
     }
@@ -765,6 +1154,27 @@ int get_tables(int device, size_t bytes, void** p) {
   *p = e.first;
   return QC_OK;
 }
+
+template <bool C128>
+int launch_reg(const qc_state* s, const TPass& P, double* partial, int grid) {
+  constexpr size_t kChunks = C128 ? ((size_t)1 << kRegL) : ((size_t)1 << (kRegL - 1));
+  const size_t smem = kChunks * 16 + ((size_t)8 << P.h);
+  static bool attr[64] = {false};
+  const int dev = s->device;
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    QC_CUDA(cudaFuncSetAttribute(k_pauli_reg<C128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kChunks * 16 + (8 << kTileMaxH))));
+    QC_CUDA(cudaFuncSetAttribute(k_pauli_reg<C128>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    if (dev >= 0 && dev < 64) attr[dev] = true;
+  }
+  k_pauli_reg<C128><<<grid, kTileThreads, smem, s->stream>>>((const unsigned char*)s->ptr, P, partial);
+  QC_LAUNCHED("k_pauli_reg");
+  return QC_OK;
+}
+
+// CTAs per SM the register-resident kernel runs with (its launch bounds)
+constexpr int reg_ctas_per_sm(bool c128) { return c128 ? 2 : 4; }
 
 template <bool C128>
 int launch_tile(const qc_state* s, const TPass& P, double* partial, int grid) {
@@ -808,10 +1218,10 @@ extern "C" int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out) 
   TilePlan plan;
   if (int rc = tile_plan(s->n, c128, terms, plan)) return rc;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  const int cap = qc_num_sms() * 3;
   std::vector<int> grids(plan.passes.size());
   size_t total = 0;
   for (size_t i = 0; i < plan.passes.size(); i++) {
+    const int cap = qc_num_sms() * (plan.passes[i].reg ? reg_ctas_per_sm(c128) : 3);
     grids[i] = (int)std::min<uint64_t>(plan.passes[i].ntiles, (uint64_t)cap);
     total += grids[i];
   }
@@ -833,8 +1243,10 @@ extern "C" int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out) 
     TPass P = plan.passes[i];
     P.terms = dterms + plan.term_off[i];
     P.groups = dgroups + plan.group_off[i];
-    const int rc = c128 ? launch_tile<true>(s, P, partial + off, grids[i])
-                        : launch_tile<false>(s, P, partial + off, grids[i]);
+    const int rc = P.reg ? (c128 ? launch_reg<true>(s, P, partial + off, grids[i])
+                                 : launch_reg<false>(s, P, partial + off, grids[i]))
+                         : (c128 ? launch_tile<true>(s, P, partial + off, grids[i])
+                                 : launch_tile<false>(s, P, partial + off, grids[i]));
     if (rc) return rc;
     off += grids[i];
   }

@@ -26,6 +26,8 @@
 #include <cstring>
 #include <type_traits>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
 #include "qc_common.cuh"
@@ -71,8 +73,11 @@ __device__ __forceinline__ void tile_vectors(const Geom& g, uint64_t b, uint64_t
 template <class Ar, int D>
 struct MatD { typename Ar::coef_t m[D * D]; };
 
+#ifndef QC_DENSE_MINB
+#define QC_DENSE_MINB 4   // resident CTAs per SM the dense sweep is compiled for
+#endif
 template <class Ar, int KH, int LOWT>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, QC_DENSE_MINB)
 k_dense(vec32* __restrict__ st, const __grid_constant__ Geom g,
         const __grid_constant__ MatD<Ar, (1 << (KH + popc_c(LOWT)))> M) {
   constexpr int KL = popc_c(LOWT);
@@ -904,6 +909,265 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL) : "memory");
 }
 
+// ---------------------------------------------------------------- fused tiles, complex128, TMA-staged
+// The complex128 tensor-core block of k_fused_tc128 with its input tiles
+// staged by the Tensor Memory Accelerator.  A block without controls below
+// the tile's run length has tiles of exactly 128 groups x 2^k members: 2^kh
+// runs of L contiguous amplitudes.  The state is described to the TMA unit as
+// a 2-D tensor of rows of 128 amplitudes (256 64-bit words), so a run is one
+// box of L / 128 rows: the CTA's elected thread starts the 2^kh box loads of
+// tile i + 1 (cp.async.bulk.tensor, completion counted on an mbarrier) as soon
+// as every thread has read tile i out of the staging buffer, and the loads
+// run while tile i's digits, MMAs and epilogue do.  No thread holds a
+// prefetched tile in registers, which leaves room for TPR threads per group
+// row.  Waits are bounded like the MMA waits; a CTA whose wait gave up stops
+// taking tiles, waits (default limit) for its TMA loads and MMAs in flight and
+// frees its tensor memory.
+struct TmaGeom {
+  uint32_t run_rows;          // L / 128
+  uint32_t nruns;             // 2^kh
+  uint32_t tile_bytes;        // 128 * 2^k * 16
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t mbar) {
+  asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+               :: "r"(dst), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(mbar) : "memory");
+}
+
+template <int K, int TPR>
+__global__ void __launch_bounds__(128 * TPR, 1)
+k_fused_tc128_tma(double2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC128<K> U,
+                  int eu, int sh, int spin, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TmaGeom tg) {
+  constexpr int D = 1 << K;
+  constexpr int NT = 128 * TPR;
+  constexpr int H = D / TPR;                      // members per thread
+  constexpr int KR = 2 * D;
+  constexpr uint32_t NCOL = kTcLev * KR <= 128 ? 128 : (kTcLev * KR <= 256 ? 256 : 512);
+  constexpr uint32_t SBO = (KR / 8) * 128;
+  constexpr uint32_t ASZ = 128 * KR * 2, BSZ = KR * KR * 2;
+  static_assert(H % 4 == 0, "four columns per store at least");
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* sA = smem_tc;                    // [digit][128 x KR] fp16
+  unsigned char* sB = sA + kTcA * ASZ;            // [digit][KR x KR] fp16
+  constexpr uint32_t XOFF = ((kTcA * ASZ + kTcB * BSZ) + 1023u) & ~1023u;
+  unsigned char* sX = smem_tc + XOFF;             // staging: the tile's runs back to back (16 B per amplitude)
+  __shared__ __align__(8) uint64_t mbar, tbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ uint32_t s_moff[D];                  // member r: amplitude offset in the staging buffer
+  __shared__ uint64_t s_gmoff[D];                 // member r: amplitude offset in the state from run 0's start
+  __shared__ int s_emax[TPR][128];
+  const int t = threadIdx.x;
+  const int w = t >> 5;
+  const int row = t & 127;
+  const int part_of = t >> 7;
+  const int m0 = part_of * H;
+  const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
+  const uint32_t tbar_a = (uint32_t)__cvta_generic_to_shared(&tbar);
+  const uint32_t sX_a = (uint32_t)__cvta_generic_to_shared(sX);
+  const double uscale = __hiloint2double((1023 + 7 - eu) << 20, 0);
+  for (int i = t; i < KR * KR; i += NT) {
+    const int n = i / KR, k = i % KR;
+    const double2 u = U.u[(n % D) * D + (k % D)];
+    double r = (n < D ? (k < D ? u.x : -u.y) : (k < D ? u.y : u.x)) * uscale;
+#pragma unroll
+    for (int s = 0; s < kTcB; s++) {
+      const double b = rint(r);
+      *reinterpret_cast<__half*>(sB + s * BSZ + kmaj16_off(n, k, KR)) = __float2half_rn((float)b);
+      r = (r - b) * 256.0;
+    }
+  }
+  const uint32_t L = 1u << g.lb;
+  if (t < D) {
+    s_moff[t] = g.run_of[t] * L + g.loff[t];
+    s_gmoff[t] = g.hoff[g.run_of[t]] + g.loff[t];
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar_a) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tbar_a) : "memory");
+  }
+  if (w == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_slot);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(dst), "r"(NCOL) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t aS = (uint32_t)__cvta_generic_to_shared(sA), bS = (uint32_t)__cvta_generic_to_shared(sB);
+  const long long rnd = sh > 0 ? 1ll << (sh - 1) : 0ll;
+  const uint32_t goff = g.goff[row];
+  // amplitude index of run 0 of tile T (the runs start on multiples of L >= 128)
+  auto run0 = [&](uint64_t T) {
+    uint64_t b = T << g.tg_log;
+    for (int i = 0; i < g.nins; i++) b = qc_insert_zero(b, g.ins[i]);
+    return (b | g.orval) & ~(uint64_t)(L - 1);
+  };
+  // elected thread: start the box loads of tile T into the staging buffer
+  auto issue_tile = [&](uint64_t T) {
+    const uint64_t r0 = run0(T);
+    mbar_expect_tx(tbar_a, tg.tile_bytes);
+    for (uint32_t h = 0; h < tg.nruns; h++)
+      tma_load_2d(sX_a + h * L * 16u, &tmap, 0, (int)((r0 + g.hoff[h]) >> 7), tbar_a);
+  };
+  uint32_t phase = 0, tphase = 0;
+  auto bar_wait = [&](uint32_t bar, uint32_t ph, int limit) {
+    uint32_t done = mbar_poll(bar, ph, limit);
+    done = __syncthreads_and(done);
+    return done != 0;
+  };
+  auto mma_wait = [&](int limit) {
+    const bool done = bar_wait(mbar_a, phase, limit);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (done) phase ^= 1u;
+    else if (t == 0) atomicAdd(&g_tc_timeouts, 1);
+    return done;
+  };
+  auto epilogue = [&](uint64_t obase, int scale, bool flush) {
+    const uint32_t lane = tmem + ((uint32_t)(32 * (w & 3)) << 16);
+    constexpr int NC = 4;
+#pragma unroll
+    for (int c = 0; c < H; c += NC) {
+      uint32_t re[kTcLev][NC], im[kTcLev][NC];
+#pragma unroll
+      for (int d = 0; d < kTcLev; d++) {
+        tmem_ld<NC>(lane + (uint32_t)(d * KR + m0 + c), re[d]);
+        tmem_ld<NC>(lane + (uint32_t)(d * KR + D + m0 + c), im[d]);
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < NC; j++) {
+        float Dr[kTcLev], Di[kTcLev];
+#pragma unroll
+        for (int d = 0; d < kTcLev; d++) { Dr[d] = __uint_as_float(re[d][j]); Di[d] = __uint_as_float(im[d][j]); }
+        st[obase + s_gmoff[m0 + c + j]] = make_double2(tc_assemble<(KR <= 32)>(Dr, sh, rnd, scale, flush),
+                                                         tc_assemble<(KR <= 32)>(Di, sh, rnd, scale, flush));
+      }
+    }
+  };
+  auto issue_mma = [&]() {
+    uint32_t lead;
+    asm volatile("{ .reg .pred p; elect.sync _|p, 0xffffffff; selp.u32 %0, 1, 0, p; }" : "=r"(lead));
+    const uint64_t adesc0 = umma_desc(aS, 128, SBO), bdesc0 = umma_desc(bS, 128, SBO);
+    const uint32_t alo = (uint32_t)adesc0, ahi = (uint32_t)(adesc0 >> 32);
+    const uint32_t blo = (uint32_t)bdesc0, bhi = (uint32_t)(bdesc0 >> 32);
+    constexpr int TMAX = 256 / KR;
+#pragma unroll
+    for (int sa = 0; sa < kTcA; sa++) {
+#pragma unroll
+      for (int t0 = 0; t0 < kTcLev - sa; t0 += TMAX) {
+        const int nt = (kTcLev - sa - t0) < TMAX ? (kTcLev - sa - t0) : TMAX;
+        const uint32_t idn = (1u << 4) | ((uint32_t)((nt * KR) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+#pragma unroll
+        for (int kk = 0; kk < KR / 16; kk++) {
+          const uint64_t ad = ((uint64_t)ahi << 32) | (alo + (uint32_t)((sa * ASZ + kk * 256) >> 4));
+          const uint64_t bd = ((uint64_t)bhi << 32) | (blo + (uint32_t)((t0 * BSZ + kk * 256) >> 4));
+          asm volatile("{ .reg .pred q, e; setp.ne.b32 q, %4, 0; setp.ne.b32 e, %5, 0;\n"
+                       "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q; }"
+                       :: "r"(tmem + (uint32_t)((sa + t0) * KR)), "l"(ad), "l"(bd), "r"(idn),
+                          "r"((sa > 0 || kk > 0) ? 1 : 0), "r"(lead) : "memory");
+        }
+      }
+    }
+    asm volatile("{ .reg .pred e; setp.ne.b32 e, %1, 0;\n"
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0]; }"
+                 :: "r"(mbar_a), "r"(lead) : "memory");
+  };
+  auto make_digits = [&](const double2* xv, bool& flush) {
+    int em = 0;
+#pragma unroll
+    for (int r = 0; r < H; r++) {
+      em = max(em, (__double2hiint(xv[r].x) >> 20) & 0x7FF);
+      em = max(em, (__double2hiint(xv[r].y) >> 20) & 0x7FF);
+    }
+    s_emax[part_of][row] = em;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TPR; i++) em = max(em, s_emax[i][row]);
+#pragma unroll
+    for (int part = 0; part < 2; part++) {
+      constexpr int CW = H >= 8 ? 8 : 4;
+#pragma unroll
+      for (int c0 = 0; c0 < H; c0 += CW) {
+        uint32_t wd[CW / 2][kTcA];
+#pragma unroll
+        for (int j = 0; j < CW; j += 2) {
+          const double va = part == 0 ? xv[c0 + j].x : xv[c0 + j].y;
+          const double vb = part == 0 ? xv[c0 + j + 1].x : xv[c0 + j + 1].y;
+          const uint32_t ha = (uint32_t)__double2hiint(va), hb = (uint32_t)__double2hiint(vb);
+          tc_digit_words(tc_window(ha, (uint32_t)__double2loint(va), em + 5),
+                         tc_window(hb, (uint32_t)__double2loint(vb), em + 5), ha, hb, wd[j / 2]);
+        }
+        const int col = part * D + m0 + c0;
+#pragma unroll
+        for (int s = 0; s < kTcA; s++) {
+          if constexpr (CW == 8)
+            *reinterpret_cast<uint4*>(sA + s * ASZ + kmaj16_off(row, col, KR)) =
+                make_uint4(wd[0][s], wd[1][s], wd[2][s], wd[3][s]);
+          else
+            *reinterpret_cast<uint2*>(sA + s * ASZ + kmaj16_off(row, col, KR)) = make_uint2(wd[0][s], wd[1][s]);
+        }
+      }
+    }
+    flush = em + eu < 64;
+    return em - 1077 + eu + sh;
+  };
+  bool ok = true;
+  bool tma_pending = false;                       // (thread 0's view) a box load is in flight
+  bool mma_pending = false;                       // MMAs committed and not yet awaited
+  if (t == 0 && blockIdx.x < g.ntiles) { issue_tile(blockIdx.x); tma_pending = true; }
+  for (uint64_t T = blockIdx.x; T < g.ntiles && ok; T += gridDim.x) {
+    // the tile's runs have landed in the staging buffer
+    if (!bar_wait(tbar_a, tphase, spin)) {
+      if (t == 0) atomicAdd(&g_tc_timeouts, 1);
+      ok = false;
+      break;
+    }
+    tphase ^= 1u;
+    if (t == 0) tma_pending = false;
+    const uint64_t cbase = run0(T) + goff;
+    double2 x[H];
+#pragma unroll
+    for (int r = 0; r < H; r++)
+      x[r] = *reinterpret_cast<const double2*>(sX + (size_t)(s_moff[m0 + r] + goff) * 16);
+    bool cflush;
+    const int cscale = make_digits(x, cflush);    // contains a __syncthreads: every thread has read sX
+    const uint64_t Tn = T + gridDim.x;
+    if (t == 0 && Tn < g.ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads before the async writes
+      issue_tile(Tn);
+      tma_pending = true;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (w == 0) issue_mma();
+    mma_pending = true;
+    ok = mma_wait(spin);
+    if (ok) {
+      mma_pending = false;
+      epilogue(cbase, cscale, cflush);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  // a wait gave up: the MMAs and box loads in flight still write this CTA's memory;
+  // wait for them (same phases, default limit) before freeing the tensor memory and exiting
+  if (!ok) {
+    if (mma_pending) mma_wait(kTcSpinDefault);
+    if (__syncthreads_or(tma_pending ? 1 : 0)) bar_wait(tbar_a, tphase, kTcSpinDefault);
+  }
+  __syncthreads();
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL) : "memory");
+}
+
 // ---------------------------------------------------------------- linear phase runs
 // A run of commuting phase gates that all involve one qubit (the QFT's
 // controlled phases after each Hadamard, Fig. 1) is one diagonal operator:
@@ -1580,6 +1844,10 @@ int launch_fused_tc_t(qc_state* s, const qc_op& op, const GeomF& g) {
   return QC_OK;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+template <int K>
+int launch_fused_tc128_tma_t(qc_state* s, const qc_op& op, const GeomF& g, int eu, int sh, const MatC128<K>& U);
+
 template <int K>
 int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
   constexpr int D = 1 << K, KR = 2 * D;
@@ -1601,6 +1869,9 @@ int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
     S = std::max(S, r);
   }
   const int sh = S > 0.0 ? std::max(0, (int)std::ceil(std::log2(S * (1.0 + 0x1p-30))) + 4 - eu) : 0;
+  // TMA-staged tiles: the tile is exactly its 128 groups (no control below the run length)
+  if (s->fused_tc == 2 && ((size_t)1 << g.lb << g.kh) == ((size_t)128 << K) && tensor_map_encoder())
+    return launch_fused_tc128_tma_t<K>(s, op, g, eu, sh, U);
   const size_t smem = (size_t)kTcA * 128 * KR * 2 + (size_t)kTcB * KR * KR * 2;
   static int per_sm_dev[64] = {};   // per device (function attributes are per device)
   const int sdev = s->device;
@@ -1627,6 +1898,84 @@ int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
   k_fused_tc128<K><<<grid, Tc128Cfg<K>::NT, smem, s->stream>>>((double2*)s->ptr, g, U, eu, sh, tc_spin(s));
   QC_LAUNCHED("k_fused_tc128");
+  return QC_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (the library does not link the driver library itself)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+#ifndef QC_TC128_TMA_TPR5
+#define QC_TC128_TMA_TPR5 4   // threads per group row of the k = 5 kernel (2: 1641 ms, 4: 1611 ms for
+                              // the n=30 brickwork at k = 5)
+#endif
+template <int K> struct Tc128TmaCfg {
+  static constexpr int TPR = K == 5 ? QC_TC128_TMA_TPR5 : 2;   // threads per group row
+  static constexpr int NT = 128 * TPR;
+};
+
+template <int K>
+int launch_fused_tc128_tma_t(qc_state* s, const qc_op& op, const GeomF& g, int eu, int sh, const MatC128<K>& U) {
+  constexpr int D = 1 << K, KR = 2 * D;
+  constexpr int TPR = Tc128TmaCfg<K>::TPR, NT = Tc128TmaCfg<K>::NT;
+  auto encode = tensor_map_encoder();
+  if (!encode) return qc_fail(QC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const uint64_t N = 1ull << s->n;
+  const uint32_t L = 1u << g.lb;
+  // the state as rows of 128 amplitudes (256 64-bit words); a run of L amplitudes is a box of L / 128 rows
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {256, (cuuint64_t)(N / 128)};
+  const cuuint64_t gstride[1] = {2048};
+  const cuuint32_t box[2] = {256, L / 128};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, s->ptr, gdim, gstride, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return qc_fail(QC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+  TmaGeom tg;
+  tg.run_rows = L / 128;
+  tg.nruns = 1u << g.kh;
+  tg.tile_bytes = 128u * D * 16u;
+  const size_t xoff = (((size_t)kTcA * 128 * KR * 2 + (size_t)kTcB * KR * KR * 2) + 1023) & ~(size_t)1023;
+  const size_t smem = xoff + (size_t)tg.tile_bytes;
+  static int per_sm_dev[64] = {};
+  const int sdev = s->device;
+  int per_sm = sdev >= 0 && sdev < 64 ? per_sm_dev[sdev] : 0;
+  if (per_sm == 0) {
+    QC_CUDA(cudaFuncSetAttribute(k_fused_tc128_tma<K, TPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QC_CUDA(cudaFuncSetAttribute(k_fused_tc128_tma<K, TPR>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    cudaFuncAttributes fa;
+    QC_CUDA(cudaFuncGetAttributes(&fa, k_fused_tc128_tma<K, TPR>));
+    int dev = 0, smem_sm = 0, regs_sm = 0;
+    QC_CUDA(cudaGetDevice(&dev));
+    QC_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    QC_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_sm / (warp_regs * (NT / 32));
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+    const int ncol = kTcLev * KR <= 128 ? 128 : (kTcLev * KR <= 256 ? 256 : 512);
+    per_sm = std::max(1, std::min(std::min(by_regs, by_smem), std::min(512 / ncol, 2048 / NT)));
+    if (sdev >= 0 && sdev < 64) per_sm_dev[sdev] = per_sm;
+  }
+  const uint64_t cap = (uint64_t)qc_num_sms() * per_sm;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, cap));
+  k_fused_tc128_tma<K, TPR><<<grid, NT, smem, s->stream>>>((double2*)s->ptr, g, U, eu, sh, tc_spin(s), map, tg);
+  QC_LAUNCHED("k_fused_tc128_tma");
   return QC_OK;
 }
 

@@ -273,9 +273,10 @@ class State:
     def set_arith(self, arith: int):
         _check(lib.qc_set_arith(self._h, arith))
 
-    def set_fused_tc(self, enable: bool):
-        """complex64 k>=3 blocks on the tensor cores (default) or CUDA cores."""
-        _check(lib.qc_set_fused_tc(self._h, int(bool(enable))))
+    def set_fused_tc(self, enable):
+        """k>=3 blocks on the tensor cores (True/1, default), on the tensor cores with
+        complex128 tiles staged by the TMA unit (2), or on the CUDA cores (False/0)."""
+        _check(lib.qc_set_fused_tc(self._h, int(enable)))
 
     def set_packed(self, enable: bool):
         """complex128 float-float sweeps with packed FP32 pairs (default) or scalar."""

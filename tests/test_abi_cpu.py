@@ -224,14 +224,14 @@ def test_count_params(q):
 
 def test_expect_pass_counts(q):
     """qc_expect's pass planning (host only): the TFIM chain's X terms on the
-    qubits above a tile's low bits need ceil((n - m) / h) passes with m = 5
-    low bits and h = 7 generators (complex128), m = 6, h = 7 (complex64);
+    qubits above a tile's low bits need ceil((n - m) / h) passes with m = 3
+    low bits and h = 9 generators (tiles of 2^12 amplitudes, both dtypes);
     states that fit one tile need one pass; one long string needs one pass;
     an empty sum none."""
     from paper_2303_00123_gb300 import circuits as C
     for n in (1, 5, 12, 13, 19, 20, 26, 30, 34):
-        for dt, m, L in ((q.C128, 5, 12), (q.C64, 6, 13)):
-            want = 1 if n <= L else -(-(n - m) // 7)
+        for dt, m, L in ((q.C128, 3, 12), (q.C64, 3, 12)):
+            want = 1 if n <= L else -(-(n - m) // (L - m))
             assert q.expect_passes(n, dt, C.tfim(n, 1.0)) == want, (n, dt)
     assert q.expect_passes(30, q.C128, [(1.0, [("X", i) for i in range(30)])]) == 1
     assert q.expect_passes(30, q.C128, [(1.0, [("Z", i) for i in range(30)])]) == 1

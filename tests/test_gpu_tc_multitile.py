@@ -112,3 +112,29 @@ def test_wait_limit_reports_timeout_and_recovers(q, dtype):
         phi = phi.astype(np.complex64).astype(np.complex128)
     ref = O.run_circuit(n, [g], phi)
     assert float(np.abs(got - ref).max()) <= (1e-12 if dt == q.C128 else 2e-5)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_tma_staged_tiles_equal_register_loads(q, k):
+    """complex128 blocks: tiles loaded by each thread (qc_set_fused_tc 1) and
+    staged by the Tensor Memory Accelerator (2) run the same arithmetic,
+    so the states agree bit for bit; both match the oracle.  Placements: low,
+    high and spread targets (TMA-staged in mode 2), and a control below the
+    run length (per-thread loads in both modes)."""
+    n = 22
+    rng = np.random.default_rng(500 + k)
+    gates = placements(rng, n, k)
+    phi = C.random_state(n, 501)
+    outs = []
+    for mode in (1, 2):
+        st = q.State(n, q.C128)
+        st.set_arith(q.ARITH_F32X2)
+        st.set_fused_tc(mode)
+        st.from_numpy(phi)
+        for g in gates:
+            st.apply_kq(g.matrix, g.qubits, g.controls, g.cstates)
+        outs.append(st.to_numpy())
+        st.free()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    ref = O.run_circuit(n, gates, phi)
+    assert float(np.abs(outs[0] - ref).max()) <= 1e-12
