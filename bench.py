@@ -87,6 +87,25 @@ def algorithmic_bytes(g, n, elem):
     return 2 * N * elem * frac
 
 
+def sector_bytes(g, n, elem):
+    """Read + write bytes of the 32-byte DRAM sectors that hold the amplitudes a
+    gate changes.  A sector holds 32 / elem amplitudes that differ in the lowest
+    one (complex128) or two (complex64) index bits, so a condition on those bits
+    (a control, the pattern of a phase gate) does not reduce the sectors moved."""
+    inb = 1 if elem == 16 else 2
+    N = 1 << n
+    pos = lambda qb: n - 1 - qb
+    name = g.name.upper()
+    cond = [pos(c) for c in g.controls]
+    if name in ("Z", "S", "SDG", "T", "TDG", "P"):
+        cond += [pos(t) for t in g.qubits]
+    frac = 1.0
+    if name == "SWAP":          # changed where the two bits differ
+        a, b = pos(g.qubits[0]), pos(g.qubits[1])
+        frac = 0.5 if (a >= inb and b >= inb) else 1.0
+    return 2 * N * elem / (1 << sum(1 for p in cond if p >= inb)) * frac
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -329,7 +348,9 @@ def run_gpu(args):
     native = None
     if not args.no_native and args.arith == "f32x2" and args.fuse == 0:
         st.set_arith(q.ARITH_NATIVE)
-        step(False)
+        for circ in (qft, brick):          # warm the native kernels on a few gates of each circuit
+            st.set_basis(x)
+            st.apply_circuit(circ[:40])
         nat_ms = []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -644,6 +665,62 @@ def run_expect_case(args):
     st.free()
 
 
+def run_shard_case(args):
+    """One n-qubit state as 2^g shards on this GPU (every shard its own state):
+    the QFT and a depth-10 brickwork through the exchange plan, against the
+    unsharded state; exchanges are in-place kernels trading half of each of two
+    shards (read + write of both halves: 2 * N * E bytes per exchange step)."""
+    import torch
+    from paper_2303_00123_gb300 import qcgb300 as q, shard
+    n, g = args.n, args.g
+    dt = q.C64 if args.dtype == "c64" else q.C128
+    elem = 8 if dt == q.C64 else 16
+    stream = torch.cuda.current_stream()
+    out = {"case": "shard", "n": n, "g": g, "dtype": args.dtype}
+    for name, circ in (("qft", C.qft(n)), ("brickwork10", C.brickwork(n, 10, seed=SEED_BRICK))):
+        steps = shard.plan(n, g, circ)
+        nex = sum(1 for st in steps if st[0] == "exchange")
+        states = [q.State(n - g, dt) for _ in range(1 << g)]
+        for st in states:
+            st.set_stream(stream)
+
+        def sharded():
+            # timing only: shard 0 restarts from its basis state, the other shards keep
+            # whatever the previous run left (the sweeps' cost does not depend on the values)
+            states[0].set_basis(0)
+            shard.run_single_device(states, n, g, steps)
+        sharded()
+        ms = _event_ms(stream, sharded)
+        # the exchanges alone: one per step, on the basis state
+        ex = [st_ for st_ in steps if st_[0] == "exchange"]
+
+        def exchanges():
+            for _, bit, local in ex:
+                for r in range(1 << g):
+                    if (r >> bit) & 1 == 0:
+                        q.shard_exchange(states[r], states[r ^ (1 << bit)], local, 0)
+        ex_ms = _event_ms(stream, exchanges) if ex else 0.0
+        for st in states:
+            st.free()
+        whole = q.State(n, dt)
+        whole.set_stream(stream)
+
+        def unsharded():
+            whole.set_basis(0)
+            whole.apply_circuit(circ)
+        unsharded()
+        ms0 = _event_ms(stream, unsharded)
+        whole.free()
+        torch.cuda.empty_cache()
+        peak, _ = measured_peaks()
+        exb = 2 * (1 << n) * elem * len(ex)
+        out[name] = {"gates": len(circ), "exchanges": nex, "sharded_ms": round(ms, 1), "unsharded_ms": round(ms0, 1),
+                     "exchange_ms": round(ex_ms, 1),
+                     "exchange_GBps": round(exb / (ex_ms * 1e-3) / 1e9, 1) if ex_ms else None,
+                     "exchange_frac_of_measured_hbm": round(exb / (ex_ms * 1e-3) / 1e9 / peak, 4) if ex_ms else None}
+    print(json.dumps(out))
+
+
 def run_case(args):
     """Per-target-qubit timing of one gate kind on an n-qubit state."""
     import torch
@@ -656,6 +733,8 @@ def run_case(args):
         return run_batch_case(args)
     if args.case == "fused":
         return run_fused_case(args)
+    if args.case == "shard":
+        return run_shard_case(args)
     n = args.n
     dt = q.C64 if args.dtype == "c64" else q.C128
     elem = 8 if dt == q.C64 else 16
@@ -679,13 +758,17 @@ def run_case(args):
     for g, m in zip(gates, per):
         b = algorithmic_bytes(g, n, elem)
         out.append({"q": g.qubits[0], "qubits": list(g.qubits), "stride": 1 << (n - 1 - g.qubits[0]), "ms": round(float(m), 4),
-                    "GBps": round(b / (m * 1e-3) / 1e9, 1)})
+                    "GBps": round(b / (m * 1e-3) / 1e9, 1),
+                    "GBps_sector": round(sector_bytes(g, n, elem) / (m * 1e-3) / 1e9, 1)})
     peak, _ = measured_peaks()
     tot_b = sum(algorithmic_bytes(g, n, elem) for g in gates)
+    tot_s = sum(sector_bytes(g, n, elem) for g in gates)
     print(json.dumps({"case": args.case, "n": n, "dtype": args.dtype, "arith": args.arith, "tc": not args.no_tc,
                       "packed": not args.no_packed,
                       "avg_GBps": round(tot_b / (per.sum() * 1e-3) / 1e9, 1),
                       "frac_of_measured_hbm": round(tot_b / (per.sum() * 1e-3) / 1e9 / peak, 4),
+                      "avg_GBps_sector": round(tot_s / (per.sum() * 1e-3) / 1e9, 1),
+                      "frac_sector": round(tot_s / (per.sum() * 1e-3) / 1e9 / peak, 4),
                       "per_target": out}))
     st.free()
 
@@ -992,6 +1075,7 @@ def main():
     ap.add_argument("--n", type=int, default=28)
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--g", type=int, default=2, help="global qubits (--case shard)")
     ap.add_argument("--n-err", dest="n_err", type=int, default=0)
     ap.add_argument("--circuit", default="brickwork", choices=["brickwork", "qft", "tfxy"])
     ap.add_argument("--no-tc", dest="no_tc", action="store_true", help="complex64 blocks on CUDA cores")
