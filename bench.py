@@ -370,10 +370,11 @@ def run_gpu(args):
     # copied host->device for every circuit, the final state device->host into a second buffer
     e2e = None
     if not args.no_e2e:
-        host_in = torch.zeros(1 << n, dtype=torch.complex128, pin_memory=True)
-        host_in[x] = 1.0
-        host_out = torch.empty(1 << n, dtype=torch.complex128, pin_memory=True)
-        in_np, out_np = host_in.numpy(), host_out.numpy()
+        # page-locked, huge-page host buffers (qcgb300.HostBuffer): the input state and the result
+        host_in = q.HostBuffer(1 << n, np.complex128)
+        host_in.array[x] = 1.0
+        host_out = q.HostBuffer(1 << n, np.complex128)
+        in_np, out_np = host_in.array, host_out.array
         e2e_steps = max(1, min(args.steps, E2E_MAX_STEPS))
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(2 * e2e_steps)]
         enqueue_s = 0.0
@@ -405,8 +406,9 @@ def run_gpu(args):
         circ_ms = sum(e[1].elapsed_time(e[2]) for e in evs) / e2e_steps
         d2h = sum(e[2].elapsed_time(e[3]) for e in evs) / e2e_steps
         wall = e2e_s / e2e_steps * 1e3
-        in_pinned = bool(host_in.is_pinned())
-        del host_in, host_out, in_np, out_np
+        del in_np, out_np
+        host_in.free()
+        host_out.free()
         bi = 2 * (1 << n) * elem
         e2e = {"value": gates_per_step * e2e_steps * world / e2e_s, "unit": "gates/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi, "steps": e2e_steps,
@@ -414,7 +416,8 @@ def run_gpu(args):
                    "wall": round(wall, 1), "h2d": round(h2d, 1), "circuits": round(circ_ms, 1), "d2h": round(d2h, 1),
                    "host_enqueue": round(enqueue_s / e2e_steps * 1e3, 1),
                    "other": round(wall - h2d - circ_ms - d2h, 1),
-                   "h2d_each_ms": h2d_each, "h2d_alone_ms": round(h2d_alone, 1), "input_pinned": in_pinned,
+                   "h2d_each_ms": h2d_each, "h2d_alone_ms": round(h2d_alone, 1),
+                   "host_buffers": "page-locked, transparent huge pages (qcgb300.HostBuffer)",
                    "note": "h2d, circuits, d2h: CUDA events on the state's stream around each phase (two circuits "
                            "per step); host_enqueue: wall time of the apply calls (marshalling, planning, launches, "
                            "overlapping the device work); other = wall - h2d - circuits - d2h"}}
@@ -669,7 +672,7 @@ def run_shard_case(args):
     """One n-qubit state as 2^g shards on this GPU (every shard its own state):
     the QFT and a depth-10 brickwork through the exchange plan, against the
     unsharded state; exchanges are in-place kernels trading half of each of two
-    shards (read + write of both halves: 2 * N * E bytes per exchange step)."""
+    shards (every shard's half read and written: N * E bytes per exchange step)."""
     import torch
     from paper_2303_00123_gb300 import qcgb300 as q, shard
     n, g = args.n, args.g
@@ -713,7 +716,7 @@ def run_shard_case(args):
         whole.free()
         torch.cuda.empty_cache()
         peak, _ = measured_peaks()
-        exb = 2 * (1 << n) * elem * len(ex)
+        exb = (1 << n) * elem * len(ex)     # each exchange reads and writes half of every shard
         out[name] = {"gates": len(circ), "exchanges": nex, "sharded_ms": round(ms, 1), "unsharded_ms": round(ms0, 1),
                      "exchange_ms": round(ex_ms, 1),
                      "exchange_GBps": round(exb / (ex_ms * 1e-3) / 1e9, 1) if ex_ms else None,

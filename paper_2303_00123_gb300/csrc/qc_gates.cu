@@ -167,43 +167,57 @@ k_perm(vec32* __restrict__ st, const __grid_constant__ Geom g) {
 // ---------------------------------------------------------------- phase
 // PH 0: general complex phase, 1: -1, 2: +i, 3: -i.
 template <class Ar, int PH>
-__global__ void __launch_bounds__(kThreads)
-k_phase(vec32* __restrict__ st, const __grid_constant__ Geom g, const typename Ar::coef_t c) {
+__device__ __forceinline__ void phase_vec(vec32& x, const Geom& g, const typename Ar::coef_t& c) {
   constexpr int V = Ar::V;
   constexpr int W = Ar::E / 4;   // words per amplitude
   constexpr int HW = W / 2;      // words per component
-  const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-  for (uint64_t j = (uint64_t)blockIdx.x * kThreads + threadIdx.x; j < g.ntiles; j += stride) {
-    const uint64_t v = tile_base(g, j);
-    vec32 x = qc_ld32(st + v);
 #pragma unroll
-    for (int e = 0; e < V; e++) {
-      if ((e & g.lowc_mask) != g.lowc_val) continue;
-      if constexpr (PH == 0) {
-        const typename Ar::val_t a = Ar::load(x, e);
-        Ar::store(x, e, Ar::template dot<1>(&c, &a));
+  for (int e = 0; e < V; e++) {
+    if ((e & g.lowc_mask) != g.lowc_val) continue;
+    if constexpr (PH == 0) {
+      const typename Ar::val_t a = Ar::load(x, e);
+      Ar::store(x, e, Ar::template dot<1>(&c, &a));
+    } else {
+      uint32_t* re = &x.w[e * W];
+      uint32_t* im = &x.w[e * W + HW];
+      if constexpr (PH == 1) {          // -x: flip both sign bits
+        re[HW - 1] ^= 0x80000000u; im[HW - 1] ^= 0x80000000u;
       } else {
-        uint32_t* re = &x.w[e * W];
-        uint32_t* im = &x.w[e * W + HW];
-        if constexpr (PH == 1) {          // -x: flip both sign bits
-          re[HW - 1] ^= 0x80000000u; im[HW - 1] ^= 0x80000000u;
-        } else {
-          uint32_t tr[HW], ti[HW];
+        uint32_t tr[HW], ti[HW];
 #pragma unroll
-          for (int w = 0; w < HW; w++) { tr[w] = re[w]; ti[w] = im[w]; }
-          if constexpr (PH == 2) {        // i*(a+ib) = -b + ia
+        for (int w = 0; w < HW; w++) { tr[w] = re[w]; ti[w] = im[w]; }
+        if constexpr (PH == 2) {        // i*(a+ib) = -b + ia
 #pragma unroll
-            for (int w = 0; w < HW; w++) { re[w] = ti[w]; im[w] = tr[w]; }
-            re[HW - 1] ^= 0x80000000u;
-          } else {                        // -i*(a+ib) = b - ia
+          for (int w = 0; w < HW; w++) { re[w] = ti[w]; im[w] = tr[w]; }
+          re[HW - 1] ^= 0x80000000u;
+        } else {                        // -i*(a+ib) = b - ia
 #pragma unroll
-            for (int w = 0; w < HW; w++) { re[w] = ti[w]; im[w] = tr[w]; }
-            im[HW - 1] ^= 0x80000000u;
-          }
+          for (int w = 0; w < HW; w++) { re[w] = ti[w]; im[w] = tr[w]; }
+          im[HW - 1] ^= 0x80000000u;
         }
       }
     }
-    qc_st32(st + v, x);
+  }
+}
+
+// Two tiles per iteration (both loads issued before either is used), so that
+// each thread keeps two 32-byte accesses in flight.
+template <class Ar, int PH>
+__global__ void __launch_bounds__(kThreads)
+k_phase(vec32* __restrict__ st, const __grid_constant__ Geom g, const typename Ar::coef_t c) {
+  const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+  for (uint64_t j = (uint64_t)blockIdx.x * kThreads + threadIdx.x; j < g.ntiles; j += 2 * stride) {
+    const uint64_t v0 = tile_base(g, j);
+    const bool two = j + stride < g.ntiles;
+    const uint64_t v1 = two ? tile_base(g, j + stride) : v0;
+    vec32 x0 = qc_ld32(st + v0);
+    vec32 x1 = qc_ld32(st + v1);
+    phase_vec<Ar, PH>(x0, g, c);
+    qc_st32(st + v0, x0);
+    if (two) {
+      phase_vec<Ar, PH>(x1, g, c);
+      qc_st32(st + v1, x1);
+    }
   }
 }
 

@@ -171,18 +171,49 @@ int plan(int n, int g, const qc_gate* gates, int ngates, std::vector<qc_shard_st
 // ---------------------------------------------------------------- kernels
 // Half of a shard: the amplitudes whose bit at position pb (pb = n_local - 1 -
 // local_qubit) equals `bit`; entry j of the half is index insert_zero(j, pb) |
-// bit << pb.  Element type: U = uint4 (one complex128 or two complex64), or
-// uint2 (one complex64) when pb = 0 splits a 16-byte pair.
+// bit << pb, counted in units of U: 32-byte vectors (two complex128 or four
+// complex64 amplitudes that share every bit but the lowest one or two) when pb
+// leaves them whole, else 16- or 8-byte units.  Two units per thread and
+// iteration, both loads issued first.
+struct alignas(32) U32 { uint4 a, b; };
+
+template <class U>
+__device__ __forceinline__ U ld_unit(const U* p) { return *p; }
+template <>
+__device__ __forceinline__ U32 ld_unit<U32>(const U32* p) {
+  const vec32 v = qc_ld32(p);
+  U32 u;
+  u.a = make_uint4(v.w[0], v.w[1], v.w[2], v.w[3]);
+  u.b = make_uint4(v.w[4], v.w[5], v.w[6], v.w[7]);
+  return u;
+}
+template <class U>
+__device__ __forceinline__ void st_unit(U* p, const U& u) { *p = u; }
+template <>
+__device__ __forceinline__ void st_unit<U32>(U32* p, const U32& u) {
+  vec32 v;
+  v.w[0] = u.a.x; v.w[1] = u.a.y; v.w[2] = u.a.z; v.w[3] = u.a.w;
+  v.w[4] = u.b.x; v.w[5] = u.b.y; v.w[6] = u.b.z; v.w[7] = u.b.w;
+  qc_st32(p, v);
+}
+
 template <class U>
 __global__ void __launch_bounds__(256)
 k_shard_swap(U* __restrict__ a, U* __restrict__ b, uint64_t nhalf, int pb, uint64_t abit, uint64_t bbit) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nhalf; j += stride) {
-    const uint64_t base = qc_insert_zero(j, pb);
-    const uint64_t ia = base | (abit << pb), ib = base | (bbit << pb);
-    const U x = a[ia], y = b[ib];
-    a[ia] = y;
-    b[ib] = x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nhalf; j += 2 * stride) {
+    const bool two = j + stride < nhalf;
+    const uint64_t b0 = qc_insert_zero(j, pb), b1 = two ? qc_insert_zero(j + stride, pb) : b0;
+    const uint64_t ia0 = b0 | (abit << pb), ib0 = b0 | (bbit << pb);
+    const uint64_t ia1 = b1 | (abit << pb), ib1 = b1 | (bbit << pb);
+    const U x0 = ld_unit(a + ia0), y0 = ld_unit(b + ib0);
+    const U x1 = ld_unit(a + ia1), y1 = ld_unit(b + ib1);
+    st_unit(a + ia0, y0);
+    st_unit(b + ib0, x0);
+    if (two) {
+      st_unit(a + ia1, y1);
+      st_unit(b + ib1, x1);
+    }
   }
 }
 
@@ -191,7 +222,7 @@ __global__ void __launch_bounds__(256)
 k_shard_pack(const U* __restrict__ s, U* __restrict__ buf, uint64_t nhalf, int pb, uint64_t bit) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nhalf; j += stride)
-    buf[j] = s[qc_insert_zero(j, pb) | (bit << pb)];
+    st_unit(buf + j, ld_unit(s + (qc_insert_zero(j, pb) | (bit << pb))));
 }
 
 template <class U>
@@ -199,24 +230,23 @@ __global__ void __launch_bounds__(256)
 k_shard_unpack(U* __restrict__ s, const U* __restrict__ buf, uint64_t nhalf, int pb, uint64_t bit) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nhalf; j += stride)
-    s[qc_insert_zero(j, pb) | (bit << pb)] = buf[j];
+    st_unit(s + (qc_insert_zero(j, pb) | (bit << pb)), ld_unit(buf + j));
 }
 
-// Units of the half: 16-byte words, each one complex128 amplitude or a pair of
-// complex64 amplitudes that share every bit but the lowest (so pb >= 1);
-// complex64 with pb = 0 moves single 8-byte amplitudes.
 struct HalfGeom {
-  bool wide;          // 16-byte units
+  int ubytes;         // 32, 16 or 8 bytes per unit
   uint64_t nhalf;     // units per half
   int pb;             // bit position in units
 };
 
 int half_geom(const qc_state* s, int local_qubit, HalfGeom& h) {
   if (local_qubit < 0 || local_qubit >= s->n) return qc_fail(QC_ERR_ARG, "local qubit %d out of range 0..%d", local_qubit, s->n - 1);
-  const int pb = s->n - 1 - local_qubit;
-  if (s->dtype == QC_C128) { h.wide = true; h.pb = pb; h.nhalf = 1ull << (s->n - 1); return QC_OK; }
-  if (pb >= 1 && s->n >= 2) { h.wide = true; h.pb = pb - 1; h.nhalf = 1ull << (s->n - 2); return QC_OK; }
-  h.wide = false;
+  const int pb = s->n - 1 - local_qubit;              // amplitude units
+  const int lv = s->dtype == QC_C128 ? 1 : 2;         // log2 amplitudes per 32-byte unit
+  const int l16 = s->dtype == QC_C128 ? 0 : 1;        // log2 amplitudes per 16-byte unit
+  if (pb >= lv && s->n - 1 >= lv) { h.ubytes = 32; h.pb = pb - lv; h.nhalf = 1ull << (s->n - 1 - lv); return QC_OK; }
+  if (pb >= l16 && s->n - 1 >= l16) { h.ubytes = 16; h.pb = pb - l16; h.nhalf = 1ull << (s->n - 1 - l16); return QC_OK; }
+  h.ubytes = 8;
   h.pb = pb;
   h.nhalf = 1ull << (s->n - 1);
   return QC_OK;
@@ -253,10 +283,13 @@ extern "C" int qc_shard_exchange(qc_state* a, qc_state* b, int local_qubit, int 
   if (int rc = half_geom(a, local_qubit, h)) return rc;
   // a's half {bit = 1 - bit_a} trades places with b's half {bit = bit_a}
   const uint64_t abit = (uint64_t)(1 - bit_a), bbit = (uint64_t)bit_a;
-  if (h.wide)
-    k_shard_swap<uint4><<<grid_of(h.nhalf), 256, 0, a->stream>>>((uint4*)a->ptr, (uint4*)b->ptr, h.nhalf, h.pb, abit, bbit);
+  const int grid = grid_of(h.nhalf / 2 + 1);
+  if (h.ubytes == 32)
+    k_shard_swap<U32><<<grid, 256, 0, a->stream>>>((U32*)a->ptr, (U32*)b->ptr, h.nhalf, h.pb, abit, bbit);
+  else if (h.ubytes == 16)
+    k_shard_swap<uint4><<<grid, 256, 0, a->stream>>>((uint4*)a->ptr, (uint4*)b->ptr, h.nhalf, h.pb, abit, bbit);
   else
-    k_shard_swap<uint2><<<grid_of(h.nhalf), 256, 0, a->stream>>>((uint2*)a->ptr, (uint2*)b->ptr, h.nhalf, h.pb, abit, bbit);
+    k_shard_swap<uint2><<<grid, 256, 0, a->stream>>>((uint2*)a->ptr, (uint2*)b->ptr, h.nhalf, h.pb, abit, bbit);
   QC_LAUNCHED("k_shard_swap");
   return QC_OK;
 }
@@ -268,8 +301,11 @@ extern "C" int qc_shard_pack(const qc_state* s, int local_qubit, int bit, void* 
   if (bit != 0 && bit != 1) return qc_fail(QC_ERR_ARG, "bit must be 0 or 1");
   HalfGeom h;
   if (int rc = half_geom(s, local_qubit, h)) return rc;
-  if (h.wide)
-    k_shard_pack<uint4><<<grid_of(h.nhalf), 256, 0, s->stream>>>((const uint4*)s->ptr, (uint4*)dev_buf, h.nhalf, h.pb, (uint64_t)bit);
+  if (h.ubytes == 32 && ((uintptr_t)dev_buf) % 32 == 0)
+    k_shard_pack<U32><<<grid_of(h.nhalf), 256, 0, s->stream>>>((const U32*)s->ptr, (U32*)dev_buf, h.nhalf, h.pb, (uint64_t)bit);
+  else if (h.ubytes >= 16)
+    k_shard_pack<uint4><<<grid_of(h.nhalf * (h.ubytes / 16)), 256, 0, s->stream>>>(
+        (const uint4*)s->ptr, (uint4*)dev_buf, h.nhalf * (h.ubytes / 16), h.pb + (h.ubytes == 32), (uint64_t)bit);
   else
     k_shard_pack<uint2><<<grid_of(h.nhalf), 256, 0, s->stream>>>((const uint2*)s->ptr, (uint2*)dev_buf, h.nhalf, h.pb, (uint64_t)bit);
   QC_LAUNCHED("k_shard_pack");
@@ -283,8 +319,11 @@ extern "C" int qc_shard_unpack(qc_state* s, int local_qubit, int bit, const void
   if (bit != 0 && bit != 1) return qc_fail(QC_ERR_ARG, "bit must be 0 or 1");
   HalfGeom h;
   if (int rc = half_geom(s, local_qubit, h)) return rc;
-  if (h.wide)
-    k_shard_unpack<uint4><<<grid_of(h.nhalf), 256, 0, s->stream>>>((uint4*)s->ptr, (const uint4*)dev_buf, h.nhalf, h.pb, (uint64_t)bit);
+  if (h.ubytes == 32 && ((uintptr_t)dev_buf) % 32 == 0)
+    k_shard_unpack<U32><<<grid_of(h.nhalf), 256, 0, s->stream>>>((U32*)s->ptr, (const U32*)dev_buf, h.nhalf, h.pb, (uint64_t)bit);
+  else if (h.ubytes >= 16)
+    k_shard_unpack<uint4><<<grid_of(h.nhalf * (h.ubytes / 16)), 256, 0, s->stream>>>(
+        (uint4*)s->ptr, (const uint4*)dev_buf, h.nhalf * (h.ubytes / 16), h.pb + (h.ubytes == 32), (uint64_t)bit);
   else
     k_shard_unpack<uint2><<<grid_of(h.nhalf), 256, 0, s->stream>>>((uint2*)s->ptr, (const uint2*)dev_buf, h.nhalf, h.pb, (uint64_t)bit);
   QC_LAUNCHED("k_shard_unpack");
