@@ -375,6 +375,7 @@ def run_gpu(args):
         host_in.array[x] = 1.0
         host_out = q.HostBuffer(1 << n, np.complex128)
         in_np, out_np = host_in.array, host_out.array
+        huge = [host_in.huge_page_bytes(), host_out.huge_page_bytes()]
         e2e_steps = max(1, min(args.steps, E2E_MAX_STEPS))
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(2 * e2e_steps)]
         enqueue_s = 0.0
@@ -418,6 +419,7 @@ def run_gpu(args):
                    "other": round(wall - h2d - circ_ms - d2h, 1),
                    "h2d_each_ms": h2d_each, "h2d_alone_ms": round(h2d_alone, 1),
                    "host_buffers": "page-locked, transparent huge pages (qcgb300.HostBuffer)",
+                   "huge_page_bytes_in_out": huge,
                    "note": "h2d, circuits, d2h: CUDA events on the state's stream around each phase (two circuits "
                            "per step); host_enqueue: wall time of the apply calls (marshalling, planning, launches, "
                            "overlapping the device work); other = wall - h2d - circuits - d2h"}}
@@ -745,7 +747,7 @@ def run_case(args):
     st = q.State.from_tensor(t)
     st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
     st.set_fused_tc(not args.no_tc)
-    st.set_packed(not args.no_packed)
+    st.set_packed(args.packed)
     stream = torch.cuda.Stream()
     st.set_stream(stream)
     st.set_basis(0)
@@ -767,7 +769,7 @@ def run_case(args):
     tot_b = sum(algorithmic_bytes(g, n, elem) for g in gates)
     tot_s = sum(sector_bytes(g, n, elem) for g in gates)
     print(json.dumps({"case": args.case, "n": n, "dtype": args.dtype, "arith": args.arith, "tc": not args.no_tc,
-                      "packed": not args.no_packed,
+                      "packed": args.packed,
                       "avg_GBps": round(tot_b / (per.sum() * 1e-3) / 1e9, 1),
                       "frac_of_measured_hbm": round(tot_b / (per.sum() * 1e-3) / 1e9 / peak, 4),
                       "avg_GBps_sector": round(tot_s / (per.sum() * 1e-3) / 1e9, 1),
@@ -1082,7 +1084,8 @@ def main():
     ap.add_argument("--n-err", dest="n_err", type=int, default=0)
     ap.add_argument("--circuit", default="brickwork", choices=["brickwork", "qft", "tfxy"])
     ap.add_argument("--no-tc", dest="no_tc", action="store_true", help="complex64 blocks on CUDA cores")
-    ap.add_argument("--no-packed", dest="no_packed", action="store_true", help="scalar FP32 float-float")
+    ap.add_argument("--packed", type=int, default=2, choices=[0, 1, 2],
+                    help="complex128 float-float form: 0 scalar, 1 packed pairs, 2 packed + 2-qubit chains")
     args = ap.parse_args()
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ and not args.case:
         # one replica rank per GPU, launched here when no launcher set the ranks up

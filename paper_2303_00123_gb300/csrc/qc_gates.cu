@@ -127,39 +127,51 @@ k_perm(vec32* __restrict__ st, const __grid_constant__ Geom g) {
   constexpr int M0 = KIND == 0 ? 0 : 1;   // the two members that trade places
   constexpr int M1 = KIND == 0 ? 1 : 2;
   const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-  for (uint64_t j = (uint64_t)blockIdx.x * kThreads + threadIdx.x; j < g.ntiles; j += stride) {
-    uint64_t vi[NV];
-    tile_vectors<KH>(g, tile_base(g, j), vi);
-    if constexpr (KL == 0) {
-      // all targets select whole vectors: move the two vectors, nothing else
-      const vec32 a = qc_ld32(st + vi[M0]);
-      const vec32 b = qc_ld32(st + vi[M1]);
+  if constexpr (KL == 0) {
+    // all targets select whole vectors: move the two vectors of each tile, nothing
+    // else; two tiles per iteration (four loads in flight before any store)
+    auto move = [&](const uint64_t* vi, vec32 a, vec32 b) {
       if (g.lowc_mask == 0) {
         qc_st32(st + vi[M0], b);
         qc_st32(st + vi[M1], a);
       } else {
-        vec32 x = a, y = b;
 #pragma unroll
         for (int e = 0; e < V; e++)
-          if ((e & g.lowc_mask) == g.lowc_val) swap_elems<E>(x, e, y, e);
-        qc_st32(st + vi[M0], x);
-        qc_st32(st + vi[M1], y);
+          if ((e & g.lowc_mask) == g.lowc_val) swap_elems<E>(a, e, b, e);
+        qc_st32(st + vi[M0], a);
+        qc_st32(st + vi[M1], b);
       }
-    } else {
-      vec32 raw[NV];
+    };
+    for (uint64_t j = (uint64_t)blockIdx.x * kThreads + threadIdx.x; j < g.ntiles; j += 2 * stride) {
+      const bool two = j + stride < g.ntiles;
+      uint64_t vi[NV], wi[NV];
+      tile_vectors<KH>(g, tile_base(g, j), vi);
+      tile_vectors<KH>(g, tile_base(g, two ? j + stride : j), wi);
+      const vec32 a0 = qc_ld32(st + vi[M0]), b0 = qc_ld32(st + vi[M1]);
+      const vec32 a1 = qc_ld32(st + wi[M0]), b1 = qc_ld32(st + wi[M1]);
+      move(vi, a0, b0);
+      if (two) move(wi, a1, b1);
+    }
+  } else {
+    for (uint64_t j = (uint64_t)blockIdx.x * kThreads + threadIdx.x; j < g.ntiles; j += stride) {
+      uint64_t vi[NV];
+      tile_vectors<KH>(g, tile_base(g, j), vi);
+      {
+        vec32 raw[NV];
 #pragma unroll
-      for (int r = 0; r < NV; r++) raw[r] = qc_ld32(st + vi[r]);
+        for (int r = 0; r < NV; r++) raw[r] = qc_ld32(st + vi[r]);
 #pragma unroll
-      for (int rest = 0; rest < V; rest++) {
-        if (rest & LOWT) continue;
-        if ((rest & g.lowc_mask) != g.lowc_val) continue;
-        constexpr int v0 = M0 >> KL, v1 = M1 >> KL;
-        const int e0 = rest | deposit_c(M0 & ((1 << KL) - 1), LOWT);
-        const int e1 = rest | deposit_c(M1 & ((1 << KL) - 1), LOWT);
-        swap_elems<E>(raw[v0], e0, raw[v1], e1);
+        for (int rest = 0; rest < V; rest++) {
+          if (rest & LOWT) continue;
+          if ((rest & g.lowc_mask) != g.lowc_val) continue;
+          constexpr int v0 = M0 >> KL, v1 = M1 >> KL;
+          const int e0 = rest | deposit_c(M0 & ((1 << KL) - 1), LOWT);
+          const int e1 = rest | deposit_c(M1 & ((1 << KL) - 1), LOWT);
+          swap_elems<E>(raw[v0], e0, raw[v1], e1);
+        }
+#pragma unroll
+        for (int r = 0; r < NV; r++) qc_st32(st + vi[r], raw[r]);
       }
-#pragma unroll
-      for (int r = 0; r < NV; r++) qc_st32(st + vi[r], raw[r]);
     }
   }
 }
@@ -218,6 +230,83 @@ k_phase(vec32* __restrict__ st, const __grid_constant__ Geom g, const typename A
       phase_vec<Ar, PH>(x1, g, c);
       qc_st32(st + v1, x1);
     }
+  }
+}
+
+// ---------------------------------------------------------------- dense 2-qubit, fixed-binade chains
+// complex128 2-qubit gate (4x4 matvec per group) with the float-float
+// products summed in a fixed-binade chain instead of TwoSum steps.  For
+// output row r, sigma = 1.5 * 2^E with 2^E at least twice S_r * max|x|
+// (S_r = sum over the row of |Re u| + |Im u|, computed on the host; max|x| =
+// the largest component among the group's four inputs, so every partial sum
+// is at most S_r * max|x| <= 2^E / 2): t <- fma(u, x, t) stays in [2^E, 2^(E+1)),
+// t - t' is exact (Sterbenz) and fma(u, x, t - t') is the step's rounding
+// error (exact up to 2^-24 of itself).  The remainders and the hi*lo cross
+// terms add up in the low word, the sum is (t - sigma) + low.  Six packed
+// FP32-pair instructions per complex half-product (the TwoSum form takes
+// twelve): the sweep is no longer bound by the FMA pipe.  Error: about
+// 2^-42 of S_r * max|x| per output (the TwoSum form: 2^-44 of the sum of the
+// |products|).
+struct ChainRows { int esr[4]; };              // ceil(log2(4 S_r)) per output row
+
+template <int KH, int LOWT>
+__global__ void __launch_bounds__(kThreads, QC_DENSE_MINB)
+k_dense2c(vec32* __restrict__ st, const __grid_constant__ Geom g, const __grid_constant__ MatD<ArC128p, 4> M,
+          const __grid_constant__ ChainRows cr) {
+  constexpr int KL = popc_c(LOWT);
+  static_assert(KH + KL == 2, "2-qubit gates");
+  constexpr int D = 4;
+  constexpr int NV = 1 << KH;
+  using P = ArC128p;
+  using val_t = P::val_t;
+  const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+  for (uint64_t j = (uint64_t)blockIdx.x * kThreads + threadIdx.x; j < g.ntiles; j += stride) {
+    uint64_t vi[NV];
+    tile_vectors<KH>(g, tile_base(g, j), vi);
+    vec32 raw[NV];
+#pragma unroll
+    for (int r = 0; r < NV; r++) raw[r] = qc_ld32(st + vi[r]);
+#pragma unroll
+    for (int rest = 0; rest < P::V; rest++) {
+      if (rest & LOWT) continue;
+      if ((rest & g.lowc_mask) != g.lowc_val) continue;
+      val_t in[D];
+      float mx = 0.f;
+#pragma unroll
+      for (int r = 0; r < D; r++) {
+        in[r] = P::load(raw[r >> KL], rest | deposit_c(r & ((1 << KL) - 1), LOWT));
+        mx = fmaxf(mx, fmaxf(fabsf(P::lo32(in[r].h)), fabsf(P::hi32(in[r].h))));
+      }
+      const int ef = (int)((__float_as_uint(mx) >> 23) & 0xFFu);
+      val_t out[D];
+#pragma unroll
+      for (int r = 0; r < D; r++) {
+        int e = ef + 1 + cr.esr[r];
+        e = e < 24 ? 24 : (e > 254 ? 254 : e);
+        const uint32_t sb = ((uint32_t)e << 23) | 0x00400000u;
+        const uint64_t sig = (uint64_t)sb | ((uint64_t)sb << 32);
+        uint64_t t = sig, lo = 0ull;
+        const P::coef_t* cf = &M.m[r * D];
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+#pragma unroll
+          for (int half = 0; half < 2; half++) {
+            // (ur, ur) * (xr, xi), then (-ui, ui) * (xi, xr)
+            const uint64_t uh = half ? cf[k].bh : cf[k].ah, ul = half ? cf[k].bl : cf[k].al;
+            const uint64_t xh = half ? P::swp(in[k].h) : in[k].h, xl = half ? P::swp(in[k].l) : in[k].l;
+            const uint64_t t1 = P::fma2(uh, xh, t);
+            const uint64_t rr = P::fma2(uh, xh, P::sub2(t, t1));
+            t = t1;
+            lo = P::fma2(ul, xh, P::fma2(uh, xl, P::add2(lo, rr)));
+          }
+        }
+        out[r] = {P::sub2(t, sig), lo};
+      }
+#pragma unroll
+      for (int r = 0; r < D; r++) P::store(raw[r >> KL], rest | deposit_c(r & ((1 << KL) - 1), LOWT), out[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < NV; r++) qc_st32(st + vi[r], raw[r]);
   }
 }
 
@@ -1590,9 +1679,35 @@ int launch_dense_t(qc_state* s, const Plan& P, const double* U) {
   return QC_OK;
 }
 
+template <int KH, int LOWT>
+int launch_dense2c_t(qc_state* s, const Plan& P, const double* U) {
+  MatD<ArC128p, 4> M;
+  ChainRows cr;
+  for (int r = 0; r < 4; r++) {
+    double S = 0.0;
+    for (int c = 0; c < 4; c++) {
+      M.m[r * 4 + c] = ArC128p::make_coef(U[2 * (r * 4 + c)], U[2 * (r * 4 + c) + 1]);
+      S += std::fabs(U[2 * (r * 4 + c)]) + std::fabs(U[2 * (r * 4 + c) + 1]);
+    }
+    // 2^esr >= 2 S (a little above, so that the coefficients' and inputs' float
+    // rounding is covered): every partial sum stays within 2^E / 2 of sigma
+    cr.esr[r] = S > 0.0 ? (int)std::ceil(std::log2(2.0 * S * (1.0 + 0x1p-10))) : -200;
+    if (S > 0.0 && (cr.esr[r] > 100 || cr.esr[r] < -100))
+      return qc_fail(QC_ERR_ARG, "matrix entries out of range for the complex128 sweep");
+  }
+  k_dense2c<KH, LOWT><<<grid_for(P.g.ntiles, kThreads), kThreads, 0, s->stream>>>((vec32*)s->ptr, P.g, M, cr);
+  QC_LAUNCHED("k_dense2c");
+  return QC_OK;
+}
+
 template <class Ar>
 int launch_dense(qc_state* s, const Plan& P, const double* U) {
   if constexpr (std::is_same<Ar, ArC128x>::value) {
+    if (s->packed == 2) {                                    // 2-qubit gates: fixed-binade chains
+      const int key2 = P.KH * 16 + P.LOWT;
+      if (key2 == 0x20) return launch_dense2c_t<2, 0>(s, P, U);
+      if (key2 == 0x11) return launch_dense2c_t<1, 1>(s, P, U);
+    }
     if (s->packed) return launch_dense<ArC128p>(s, P, U);   // same arithmetic, packed FP32 pairs
   }
   const int key = P.KH * 16 + P.LOWT;

@@ -82,7 +82,7 @@ static int new_handle(void* ptr, int n, int dtype, int owned, qc_state** out) {
   s->owned = owned;
   s->arith = QC_ARITH_AUTO;
   s->fused_tc = 1;
-  s->packed = 1;
+  s->packed = 2;
   s->wait_limit = 0;
   s->stream = nullptr;
   cudaGetDevice(&s->device);
@@ -206,7 +206,8 @@ int qc_set_fused_tc(qc_state* s, int enable) {
 
 int qc_set_packed(qc_state* s, int enable) {
   if (!s) return qc_fail(QC_ERR_ARG, "state handle is NULL");
-  s->packed = enable ? 1 : 0;
+  if (enable < 0 || enable > 2) return qc_fail(QC_ERR_ARG, "qc_set_packed: enable must be 0, 1 or 2");
+  s->packed = enable;
   return QC_OK;
 }
 

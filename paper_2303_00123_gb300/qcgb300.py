@@ -242,6 +242,22 @@ class HostBuffer:
             raise QCError(QC_ERR_CUDA, "cudaHostRegister failed: %s" % err)
         self._registered = True
 
+    def huge_page_bytes(self) -> int:
+        """Bytes of the buffer backed by transparent huge pages (Linux smaps)."""
+        lo_addr, tot, inside = self._ptr, 0, False
+        try:
+            with open("/proc/self/smaps") as f:
+                for ln in f:
+                    parts = ln.split()
+                    if parts and "-" in parts[0] and ":" not in parts[0]:
+                        a, b = (int(x, 16) for x in parts[0].split("-"))
+                        inside = a < lo_addr + self.nbytes and b > lo_addr
+                    elif inside and parts and parts[0] == "AnonHugePages:":
+                        tot += int(parts[1]) * 1024
+        except OSError:
+            return -1
+        return tot
+
     def free(self):
         if getattr(self, "_registered", False):
             import torch
@@ -324,9 +340,10 @@ class State:
         complex128 tiles staged by the TMA unit (2), or on the CUDA cores (False/0)."""
         _check(lib.qc_set_fused_tc(self._h, int(enable)))
 
-    def set_packed(self, enable: bool):
-        """complex128 float-float sweeps with packed FP32 pairs (default) or scalar."""
-        _check(lib.qc_set_packed(self._h, int(bool(enable))))
+    def set_packed(self, enable):
+        """complex128 float-float sweeps: scalar FP32 (0/False), packed FP32 pairs (1/True),
+        packed with fixed-binade chains for dense 2-qubit gates (2, the default)."""
+        _check(lib.qc_set_packed(self._h, int(enable)))
 
     def set_wait_limit(self, polls: int):
         """Tensor-core MMA wait limit in polls (0: default; < 0: no poll, for tests)."""
