@@ -247,7 +247,44 @@ k_phase(vec32* __restrict__ st, const __grid_constant__ Geom g, const typename A
 // twelve): the sweep is no longer bound by the FMA pipe.  Error: about
 // 2^-42 of S_r * max|x| per output (the TwoSum form: 2^-44 of the sum of the
 // |products|).
-struct ChainRows { int esr[4]; };              // ceil(log2(4 S_r)) per output row
+struct ChainRows { int esr[4]; };              // ceil(log2(2 S_r (1 + 2^-10))) per output row
+
+// sigma = 1.5 * 2^E, E = biased exponent e (clamped to normal floats), as a packed pair
+__device__ __forceinline__ uint64_t chain_sigma2(int e) {
+  e = e < 24 ? 24 : (e > 254 ? 254 : e);
+  const uint32_t sb = ((uint32_t)e << 23) | 0x00400000u;
+  return (uint64_t)sb | ((uint64_t)sb << 32);
+}
+
+// sum_k cf[k] * x[k] (complex, packed pairs) in a fixed-binade chain started at sig
+template <int K>
+__device__ __forceinline__ ArC128p::val_t chain_dot(const ArC128p::coef_t* cf, const ArC128p::val_t* x, uint64_t sig) {
+  using P = ArC128p;
+  uint64_t t = sig, lo = 0ull;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+      const uint64_t uh = half ? cf[k].bh : cf[k].ah, ul = half ? cf[k].bl : cf[k].al;
+      const uint64_t xh = half ? P::swp(x[k].h) : x[k].h, xl = half ? P::swp(x[k].l) : x[k].l;
+      const uint64_t t1 = P::fma2(uh, xh, t);
+      const uint64_t rr = P::fma2(uh, xh, P::sub2(t, t1));
+      t = t1;
+      lo = P::fma2(ul, xh, P::fma2(uh, xl, P::add2(lo, rr)));
+    }
+  }
+  return {P::sub2(t, sig), lo};
+}
+
+// biased exponent of the largest component (hi parts) of K packed inputs
+template <int K>
+__device__ __forceinline__ int chain_exp(const ArC128p::val_t* x) {
+  float mx = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; k++)
+    mx = fmaxf(mx, fmaxf(fabsf(ArC128p::lo32(x[k].h)), fabsf(ArC128p::hi32(x[k].h))));
+  return (int)((__float_as_uint(mx) >> 23) & 0xFFu);
+}
 
 template <int KH, int LOWT>
 __global__ void __launch_bounds__(kThreads, QC_DENSE_MINB)
@@ -1391,11 +1428,14 @@ struct DLTab {
   typename Ar::coef_t w[Ar::V * kDlR];
 };
 
-template <class Ar, int R>
+// CHAIN (packed complex128 only): the two rows and the window phase sum their
+// products in fixed-binade chains (see k_dense2c); esr = ceil(log2(2 S_r (1 +
+// 2^-10))) of U's rows, the window phase (|w| = 1) taking row 1's plus one.
+template <class Ar, int R, bool CHAIN = false>
 __global__ void __launch_bounds__(kThreads, 2)
 k_dense_linphase(vec32* __restrict__ st, const __grid_constant__ DLGeom dg, const __grid_constant__ MatD<Ar, 2> M,
                  const __grid_constant__ MatD<typename HiAr<Ar>::type, 2> Mh, const __grid_constant__ DLTab<Ar> tab,
-                 int nhi) {
+                 int nhi, int esr0, int esr1) {
   constexpr int V = Ar::V;
   constexpr int L = V == 4 ? 2 : 1;
   using Hi = typename HiAr<Ar>::type;
@@ -1435,9 +1475,17 @@ k_dense_linphase(vec32* __restrict__ st, const __grid_constant__ DLGeom dg, cons
 #pragma unroll
       for (int e = 0; e < V; e++) {
         val_t in[2] = {Ar::load(r0[k], e), Ar::load(r1[k], e)};
-        const val_t o0 = Ar::template dot<2>(&M.m[0], in);
-        val_t o1 = Ar::template dot<2>(row1, in);
-        o1 = Ar::template dot<1>(&Tw[k * V + e], &o1);
+        val_t o0, o1;
+        if constexpr (CHAIN) {
+          const int ef = chain_exp<2>(in);
+          o0 = chain_dot<2>(&M.m[0], in, chain_sigma2(ef + 1 + esr0));
+          o1 = chain_dot<2>(row1, in, chain_sigma2(ef + 1 + esr1));
+          o1 = chain_dot<1>(&Tw[k * V + e], &o1, chain_sigma2(ef + 2 + esr1));
+        } else {
+          o0 = Ar::template dot<2>(&M.m[0], in);
+          o1 = Ar::template dot<2>(row1, in);
+          o1 = Ar::template dot<1>(&Tw[k * V + e], &o1);
+        }
         Ar::store(r0[k], e, o0);
         Ar::store(r1[k], e, o1);
       }
@@ -2246,7 +2294,23 @@ int launch_dense_linphase(qc_state* s, const qc_op& op) {
   const uint64_t nruns = P.g.ntiles / R;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((nruns + kThreads - 1) / kThreads,
                                                                    (uint64_t)qc_num_sms() * 8));
-  k_dense_linphase<Ar, R><<<grid, kThreads, 0, s->stream>>>((vec32*)s->ptr, dg, M, Mh, *tab, ntab);
+  if constexpr (std::is_same<Ar, ArC128p>::value) {
+    if (s->packed == 2) {            // fixed-binade chains: exponent offsets of U's rows
+      int esr[2];
+      for (int r = 0; r < 2; r++) {
+        double S = 0.0;
+        for (int c = 0; c < 2; c++) S += std::fabs(op.U[2 * (2 * r + c)]) + std::fabs(op.U[2 * (2 * r + c) + 1]);
+        esr[r] = S > 0.0 ? (int)std::ceil(std::log2(2.0 * S * (1.0 + 0x1p-10))) : -200;
+        if (S > 0.0 && (esr[r] > 100 || esr[r] < -100))
+          return qc_fail(QC_ERR_ARG, "matrix entries out of range for the complex128 sweep");
+      }
+      k_dense_linphase<Ar, R, true><<<grid, kThreads, 0, s->stream>>>((vec32*)s->ptr, dg, M, Mh, *tab, ntab,
+                                                                       esr[0], esr[1]);
+      QC_LAUNCHED("k_dense_linphase");
+      return QC_OK;
+    }
+  }
+  k_dense_linphase<Ar, R><<<grid, kThreads, 0, s->stream>>>((vec32*)s->ptr, dg, M, Mh, *tab, ntab, 0, 0);
   QC_LAUNCHED("k_dense_linphase");
   return QC_OK;
 }
