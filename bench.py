@@ -586,7 +586,7 @@ def run_fused_case(args):
     t = torch.empty(1 << n, dtype=torch.complex64 if dt == q.C64 else torch.complex128, device="cuda")
     st = q.State.from_tensor(t)
     st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
-    st.set_fused_tc(not args.no_tc)
+    st.set_fused_tc(0 if args.no_tc else args.tc_mode)
     stream = torch.cuda.Stream()
     st.set_stream(stream)
     res = {}
@@ -619,7 +619,7 @@ def run_fused_case(args):
         for k in ks:
             s2 = q.State(ne, dt)
             s2.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
-            s2.set_fused_tc(not args.no_tc)
+            s2.set_fused_tc(0 if args.no_tc else args.tc_mode)
             s2.apply_circuit(g2, fuse_k=k)
             got = s2.to_numpy().astype(np.complex128)
             s2.free()
@@ -746,7 +746,7 @@ def run_case(args):
     t = torch.zeros(1 << n, dtype=torch.complex64 if dt == q.C64 else torch.complex128, device="cuda")
     st = q.State.from_tensor(t)
     st.set_arith(q.ARITH_F32X2 if args.arith == "f32x2" else q.ARITH_NATIVE)
-    st.set_fused_tc(not args.no_tc)
+    st.set_fused_tc(0 if args.no_tc else args.tc_mode)
     st.set_packed(args.packed)
     stream = torch.cuda.Stream()
     st.set_stream(stream)
@@ -1084,6 +1084,8 @@ def main():
     ap.add_argument("--n-err", dest="n_err", type=int, default=0)
     ap.add_argument("--circuit", default="brickwork", choices=["brickwork", "qft", "tfxy"])
     ap.add_argument("--no-tc", dest="no_tc", action="store_true", help="complex64 blocks on CUDA cores")
+    ap.add_argument("--tc-mode", dest="tc_mode", type=int, default=1, choices=[1, 2, 3, 4],
+                    help="tensor-core block kernel (qc_set_fused_tc) of the micro-benchmarks")
     ap.add_argument("--packed", type=int, default=2, choices=[0, 1, 2],
                     help="complex128 float-float form: 0 scalar, 1 packed pairs, 2 packed + 2-qubit chains")
     args = ap.parse_args()

@@ -106,17 +106,26 @@ int qc_set_stream(qc_state* s, void* cuda_stream);
 int qc_set_arith(qc_state* s, int arith);
 
 /* Dense blocks on k = 3..5 qubits (fused gates, qc_apply_kq) run on the
- * tensor cores when enable != 0 (the default, 1), else on the CUDA cores:
- * complex64 with split-TF32 products (hi*hi + hi*lo + lo*hi, FP32
- * accumulators); complex128 under QC_ARITH_F32X2 with exact fp16 digit slices
- * (entries rounded to 48 bits against their group's largest exponent, six
- * base-2^8 digits; the matrix in seven; exact integer level sums; error about
- * 2^-47 of each 128-group's largest amplitude).  enable = 2: complex128
- * blocks whose tile holds exactly its groups (no control below the tile's run
- * length) have their tiles staged by the Tensor Memory Accelerator instead of
- * per-thread loads -- the same arithmetic and bit-identical results, measured
- * slower (the staging buffer's traffic competes with the MMAs' operand reads
- * for shared-memory bandwidth), so 1, per-thread loads, is the default. */
+ * tensor cores when enable != 0, else on the CUDA cores: complex64 with
+ * split-TF32 products (hi*hi + hi*lo + lo*hi, FP32 accumulators); complex128
+ * under QC_ARITH_F32X2 with exact fp16 digit slices (entries rounded to 48
+ * bits against their group's largest exponent, six base-2^8 digits; the
+ * matrix in seven; exact integer level sums; error about 2^-47 of each
+ * 128-group's largest amplitude).  Every choice below computes the same
+ * products in the same accumulators, so results are bit-identical; they differ
+ * only in how a tile's work is scheduled:
+ *   enable = 1 (the default): complex128 blocks on k = 4, 5 qubits in the
+ *     warp-specialised pipeline (producer warps make the next tile's digits,
+ *     an MMA warp and epilogue warps work on other tiles at the same time);
+ *     complex128 k = 3 and all complex64 blocks in the one-role kernel (all
+ *     warps load, split, wait for the MMAs and store; two CTAs per SM) --
+ *     the faster of the two for each, as measured;
+ *   enable = 2: the one-role kernel, with the tiles of complex128 blocks that
+ *     hold exactly their groups (no control below the tile's run length)
+ *     staged by the Tensor Memory Accelerator -- measured slower (the staging
+ *     buffer's traffic competes with the MMAs' operand reads);
+ *   enable = 3: the pipeline for every block of both types;
+ *   enable = 4: the one-role kernel for every block. */
 int qc_set_fused_tc(qc_state* s, int enable);
 
 /* complex128 float-float dense and phase sweeps: enable = 0 scalar FP32

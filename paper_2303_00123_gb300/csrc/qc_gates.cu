@@ -1049,6 +1049,506 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL) : "memory");
 }
 
+// ---------------------------------------------------------------- fused tiles, complex128, warp-specialised
+// The complex128 tensor-core block of k_fused_tc128 (same digits, same 27
+// products, same integer epilogue, bit-identical results) as a pipeline of
+// warp roles that work on different tiles at once, so that digit-making, the
+// MMAs and the epilogue overlap instead of following one another:
+//  * 8 producer warps, two threads per group (lanes 2g and 2g + 1 hold members
+//    [0, D/2) and [D/2, D) of group g; the pair shares the group exponent by a
+//    shuffle): a thread loads its members of tile i + 1 while tile i is in the
+//    tensor cores and writes their digits once the A buffer is free again;
+//  * 1 MMA warp: per tile and per accumulator part the digit-run MMAs of
+//    k_fused_tc128 into a ring of accumulator slots.  A part is the outputs of
+//    D / NP members in all 7 levels; k = 5 has two (7 x 32 columns each, two
+//    slots), so the MMAs of one half overlap the epilogue of the other;
+//  * 8 epilogue warps, two per tensor-memory lane quarter (each half of a
+//    part's members): read a finished part, hand its slot back, assemble and
+//    store the doubles.
+// Hand-offs are mbarriers: A full (producers -> MMA warp), A empty (MMA commit
+// -> producers), part full (MMA commit -> epilogue), part empty (epilogue ->
+// MMA warp), and the rows' scales per tile (producers -> epilogue, with an
+// empty barrier for reuse).  Every wait polls with a limit and is decided for
+// the whole warp; a wait that reaches the limit raises the CTA's abort flag
+// (counted once in g_tc_timeouts), which ends every role's loop; before the
+// tensor memory is freed the MMA warp waits for the MMAs it committed.
+constexpr int kTcFlushScale = -0x7fffffff - 1;   // row scale of a group whose outputs are zero
+
+template <int K> struct Tc128WsCfg {
+  static constexpr int D = 1 << K, KR = 2 * D;
+  static constexpr int NP = K == 5 ? 2 : 1;           // accumulator parts per tile
+  static constexpr int PM = D / NP;                   // members per part
+  static constexpr int PC = 2 * PM;                   // columns per level and part (Re, Im)
+  static constexpr int PCOLS = kTcLev * PC;           // tensor-memory columns per part
+  static constexpr int NTS = 512 / PCOLS;             // accumulator slots (k = 5, 4: 2; k = 3: 4)
+  static constexpr int NA = K == 5 ? 1 : (K == 4 ? 3 : 4);   // A buffers (96 / 48 / 24 KB each)
+  static constexpr int NMS = 4;                       // row-scale slots
+  static constexpr int H = D / 2;                     // members per producer thread
+  static constexpr int EM = PM / 2;                   // members per epilogue thread and part
+  static constexpr int NTH = 17 * 32;                 // 8 producer + 8 epilogue warps + the MMA warp
+  static constexpr uint32_t ASZ = 128u * KR * 2;      // bytes per state digit slice
+  static constexpr uint32_t ASZT = kTcA * ASZ;        // bytes per A buffer
+  static constexpr uint32_t BPZ = kTcB * PC * KR * 2; // bytes of matrix digits per part
+  static constexpr size_t SMEM = (size_t)NA * ASZT + (size_t)NP * BPZ;
+};
+
+// Poll an mbarrier phase for up to `limit` tries, giving up early when the
+// CTA's abort flag is raised; the outcome is decided for the whole warp (all
+// lanes must be present).  A wait that reaches its limit raises the flag and
+// counts one time-out for the CTA.
+__device__ __forceinline__ bool ws_wait(uint32_t bar, uint32_t parity, int limit, int* abort_flag) {
+  uint32_t done = 0;
+  for (int it = 0; it < limit && !done; it++) {
+    asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (!done && (it & 31) == 31 && *(volatile int*)abort_flag) break;
+  }
+  done = __all_sync(0xffffffffu, done);
+  if (!done && (threadIdx.x & 31) == 0) {
+    if (atomicExch(abort_flag, 1) == 0) atomicAdd(&g_tc_timeouts, 1);
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void ws_arrive(uint32_t bar) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" :: "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void ws_commit(uint32_t bar, uint32_t lead) {
+  asm volatile("{ .reg .pred e; setp.ne.b32 e, %1, 0;\n"
+               "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0]; }"
+               :: "r"(bar), "r"(lead) : "memory");
+}
+
+template <int K>
+__global__ void __launch_bounds__(Tc128WsCfg<K>::NTH, 1)
+k_fused_tc128_ws(double2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC128<K> U,
+                 int eu, int sh, int spin) {
+  using C = Tc128WsCfg<K>;
+  constexpr int D = C::D, KR = C::KR, NP = C::NP, PM = C::PM, PC = C::PC, H = C::H, EM = C::EM;
+  constexpr int NA = C::NA, NTS = C::NTS, NMS = C::NMS;
+  constexpr uint32_t SBO = (KR / 8) * 128;
+  extern __shared__ __align__(1024) unsigned char smem_ws[];
+  unsigned char* sA = smem_ws;                        // [buffer][digit][128 x KR] fp16
+  unsigned char* sB = sA + NA * C::ASZT;              // [part][digit][PC rows x KR] fp16
+  __shared__ __align__(8) uint64_t bar_af[NA], bar_ae[NA], bar_tf[NTS], bar_te[NTS], bar_mf[NMS], bar_me[NMS];
+  __shared__ __align__(8) uint64_t bar_drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+  __shared__ int s_scale[NMS][128];
+  __shared__ uint64_t s_moff[D];
+  __shared__ uint64_t s_pmoff[2][H + 1];          // producers' copy, rows apart by an odd word pair
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  auto sh_addr = [](const void* p) { return (uint32_t)__cvta_generic_to_shared(p); };
+  // matrix digits: B row r of part p and digit s is output n = (r < PM ? p PM + r : D + p PM + r - PM)
+  const double uscale = __hiloint2double((1023 + 7 - eu) << 20, 0);
+  for (int i = t; i < KR * KR; i += C::NTH) {
+    const int n = i / KR, k = i % KR;
+    const double2 u = U.u[(n % D) * D + (k % D)];
+    double r = (n < D ? (k < D ? u.x : -u.y) : (k < D ? u.y : u.x)) * uscale;
+    const int mem = n % D, p = mem / PM, rr = (n < D ? 0 : PM) + mem % PM;
+#pragma unroll
+    for (int s = 0; s < kTcB; s++) {
+      const double b = rint(r);
+      *reinterpret_cast<__half*>(sB + kmaj16_off((p * kTcB + s) * PC + rr, k, KR)) = __float2half_rn((float)b);
+      r = (r - b) * 256.0;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (t < D) s_moff[t] = s_pmoff[t / H][t % H] = g.hoff[g.run_of[t]] + g.loff[t];
+  if (t == 0) {
+    s_abort = 0;
+    auto init = [](uint64_t* b, uint32_t count) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"((uint32_t)__cvta_generic_to_shared(b)), "r"(count)
+                   : "memory");
+    };
+    for (int a = 0; a < NA; a++) { init(&bar_af[a], 256); init(&bar_ae[a], 1); }
+    for (int j = 0; j < NTS; j++) { init(&bar_tf[j], 1); init(&bar_te[j], 256); }
+    for (int j = 0; j < NMS; j++) { init(&bar_mf[j], 256); init(&bar_me[j], 256); }
+    init(&bar_drain, 1);
+  }
+  if (w == 16) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(sh_addr(&tmem_slot)), "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t L = 1u << g.lb;
+  auto tile_base = [&](uint64_t T) {
+    uint64_t b = T << g.tg_log;
+    for (int i = 0; i < g.nins; i++) b = qc_insert_zero(b, g.ins[i]);
+    return (b | g.orval) & ~(uint64_t)(L - 1);
+  };
+
+  if (w < 8) {
+    // ------------------------------------------------ producers
+    const int row = t >> 1, m0 = (t & 1) * H;
+    const uint64_t goff = g.goff[row];
+    // this tile's members; the next tile's are loaded once these are in the A buffer
+    double2 x[H];
+    uint64_t T = blockIdx.x;
+    if (T < g.ntiles) {
+      const uint64_t base = tile_base(T) + goff;
+#pragma unroll
+      for (int r = 0; r < H; r++) x[r] = st[base + s_pmoff[t & 1][r]];
+    }
+    for (int i = 0; T < g.ntiles; i++, T += gridDim.x) {
+      int em = 0;
+#pragma unroll
+      for (int r = 0; r < H; r++) {
+        em = max(em, (__double2hiint(x[r].x) >> 20) & 0x7FF);
+        em = max(em, (__double2hiint(x[r].y) >> 20) & 0x7FF);
+      }
+      em = max(em, __shfl_xor_sync(0xffffffffu, em, 1));
+      const int a = i % NA;
+      if (i >= NA && !ws_wait(sh_addr(&bar_ae[a]), (uint32_t)((i / NA - 1) & 1), spin, &s_abort)) break;
+      unsigned char* sAa = sA + a * C::ASZT;
+      // Re -> column m0 + r, Im -> column D + m0 + r; 16-byte stores (8 columns) where the thread has them
+#pragma unroll
+      for (int comp = 0; comp < 2; comp++) {
+        constexpr int CW = H >= 8 ? 8 : 4;
+#pragma unroll
+        for (int c0 = 0; c0 < H; c0 += CW) {
+          uint32_t wd[CW / 2][kTcA];
+#pragma unroll
+          for (int j = 0; j < CW; j += 2) {
+            const double va = comp == 0 ? x[c0 + j].x : x[c0 + j].y;
+            const double vb = comp == 0 ? x[c0 + j + 1].x : x[c0 + j + 1].y;
+            const uint32_t ha = (uint32_t)__double2hiint(va), hb = (uint32_t)__double2hiint(vb);
+            tc_digit_words(tc_window(ha, (uint32_t)__double2loint(va), em + 5),
+                           tc_window(hb, (uint32_t)__double2loint(vb), em + 5), ha, hb, wd[j / 2]);
+          }
+          const int col = comp * D + m0 + c0;
+#pragma unroll
+          for (int s = 0; s < kTcA; s++) {
+            if constexpr (CW == 8)
+              *reinterpret_cast<uint4*>(sAa + s * C::ASZ + kmaj16_off(row, col, KR)) =
+                  make_uint4(wd[0][s], wd[1][s], wd[2][s], wd[3][s]);
+            else
+              *reinterpret_cast<uint2*>(sAa + s * C::ASZ + kmaj16_off(row, col, KR)) = make_uint2(wd[0][s], wd[1][s]);
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      ws_arrive(sh_addr(&bar_af[a]));
+      // the row's output scale (value = sum * 2^(E - 1077 + eu), E the exponent field; groups below 2^-959 give zero)
+      const int ms = i % NMS;
+      if (i >= NMS && !ws_wait(sh_addr(&bar_me[ms]), (uint32_t)((i / NMS - 1) & 1), spin, &s_abort)) break;
+      if ((t & 1) == 0) s_scale[ms][row] = em + eu < 64 ? kTcFlushScale : em - 1077 + eu + sh;
+      ws_arrive(sh_addr(&bar_mf[ms]));
+      const uint64_t Tn = T + gridDim.x;
+      if (Tn < g.ntiles) {
+        const uint64_t base = tile_base(Tn) + goff;
+#pragma unroll
+        for (int r = 0; r < H; r++) x[r] = st[base + s_pmoff[t & 1][r]];
+      }
+    }
+  } else if (w < 16) {
+    // ------------------------------------------------ epilogue
+    const int q = w & 3, ep = (w - 8) >> 2;
+    const int row = 32 * q + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+    const uint64_t goff = g.goff[row];
+    const long long rnd = sh > 0 ? 1ll << (sh - 1) : 0ll;
+    bool go = true;
+    uint64_t T = blockIdx.x;
+    for (int i = 0; go && T < g.ntiles; i++, T += gridDim.x) {
+      const int ms = i % NMS;
+      if (!ws_wait(sh_addr(&bar_mf[ms]), (uint32_t)((i / NMS) & 1), spin, &s_abort)) break;
+      const int sc = s_scale[ms][row];
+      ws_arrive(sh_addr(&bar_me[ms]));
+      const bool flush = sc == kTcFlushScale;
+      const uint64_t obase = tile_base(T) + goff;
+#pragma unroll 1
+      for (int p = 0; p < NP; p++) {
+        const int j = i * NP + p, slot = j % NTS;
+        if (!ws_wait(sh_addr(&bar_tf[slot]), (uint32_t)((j / NTS) & 1), spin, &s_abort)) { go = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t pbase = lane_base + (uint32_t)(slot * C::PCOLS + ep * EM);
+        constexpr int NC = 4;
+#pragma unroll
+        for (int c = 0; c < EM; c += NC) {
+          uint32_t re[kTcLev][NC], im[kTcLev][NC];
+#pragma unroll
+          for (int d = 0; d < kTcLev; d++) {
+            tmem_ld<NC>(pbase + (uint32_t)(d * PC + c), re[d]);
+            tmem_ld<NC>(pbase + (uint32_t)(d * PC + PM + c), im[d]);
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (c + NC >= EM) {
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            ws_arrive(sh_addr(&bar_te[slot]));
+          }
+#pragma unroll
+          for (int jj = 0; jj < NC; jj++) {
+            float Dr[kTcLev], Di[kTcLev];
+#pragma unroll
+            for (int d = 0; d < kTcLev; d++) { Dr[d] = __uint_as_float(re[d][jj]); Di[d] = __uint_as_float(im[d][jj]); }
+            st[obase + s_moff[p * PM + ep * EM + c + jj]] =
+                make_double2(tc_assemble<(KR <= 32)>(Dr, sh, rnd, sc, flush), tc_assemble<(KR <= 32)>(Di, sh, rnd, sc, flush));
+          }
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------ MMA warp
+    uint32_t lead;
+    asm volatile("{ .reg .pred p; elect.sync _|p, 0xffffffff; selp.u32 %0, 1, 0, p; }" : "=r"(lead));
+    const uint32_t aS = sh_addr(sA), bS = sh_addr(sB);
+    const uint64_t adesc0 = umma_desc(aS, 128, SBO), bdesc0 = umma_desc(bS, 128, SBO);
+    const uint32_t alo = (uint32_t)adesc0, ahi = (uint32_t)(adesc0 >> 32);
+    const uint32_t blo = (uint32_t)bdesc0, bhi = (uint32_t)(bdesc0 >> 32);
+    bool go = true;
+    uint64_t T = blockIdx.x;
+    for (int i = 0; go && T < g.ntiles; i++, T += gridDim.x) {
+      const int a = i % NA;
+      if (!ws_wait(sh_addr(&bar_af[a]), (uint32_t)((i / NA) & 1), spin, &s_abort)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int p = 0; p < NP; p++) {
+        const int j = i * NP + p, slot = j % NTS;
+        if (j >= NTS && !ws_wait(sh_addr(&bar_te[slot]), (uint32_t)((j / NTS - 1) & 1), spin, &s_abort)) {
+          go = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // state digit sa against matrix digits 0 .. 6 - sa: one MMA per K step, N = (7 - sa) PC,
+        // accumulator columns from level sa
+#pragma unroll
+        for (int sa = 0; sa < kTcA; sa++) {
+          const int nt = kTcLev - sa;
+          const uint32_t idn = (1u << 4) | ((uint32_t)((nt * PC) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+#pragma unroll
+          for (int kk = 0; kk < KR / 16; kk++) {
+            const uint64_t ad = ((uint64_t)ahi << 32) | (alo + (uint32_t)((a * C::ASZT + sa * C::ASZ + kk * 256) >> 4));
+            const uint64_t bd = ((uint64_t)bhi << 32) | (blo + (uint32_t)((p * C::BPZ + kk * 256) >> 4));
+            asm volatile("{ .reg .pred q, e; setp.ne.b32 q, %4, 0; setp.ne.b32 e, %5, 0;\n"
+                         "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q; }"
+                         :: "r"(tmem + (uint32_t)(slot * C::PCOLS + sa * PC)), "l"(ad), "l"(bd), "r"(idn),
+                            "r"((sa > 0 || kk > 0) ? 1 : 0), "r"(lead) : "memory");
+          }
+        }
+        ws_commit(sh_addr(&bar_tf[slot]), lead);
+      }
+      if (go) ws_commit(sh_addr(&bar_ae[a]), lead);
+    }
+    // every committed MMA has finished before the tensor memory is freed
+    ws_commit(sh_addr(&bar_drain), lead);
+    mbar_poll(sh_addr(&bar_drain), 0, kTcSpinDefault);
+    __syncwarp();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 16) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- fused tiles, complex64, warp-specialised
+// The complex64 tensor-core block of k_fused_tc (split TF32, the same three
+// products into the same two accumulators, identical results) with the warp
+// roles of k_fused_tc128_ws: 8 producer warps (lanes 2g, 2g + 1: the two
+// halves of group g's members) load tile i + 1 and write its hi/lo operands
+// into a free A buffer; the MMA warp runs the tile's MMAs into one of four
+// accumulator slots (2 KR columns each); 8 epilogue warps (two per lane
+// quarter) add the two accumulators of a finished slot, hand it back and
+// store.  Hand-offs and bounded waits as in k_fused_tc128_ws.
+template <int K> struct TcWsCfg {
+  static constexpr int D = 1 << K, KR = 2 * D;
+  static constexpr int ACOLS = 2 * KR;                // hi*hi and the cross products
+  static constexpr int NTS = 4;                       // accumulator slots
+  static constexpr uint32_t NCOL = NTS * ACOLS < 32 ? 32 : NTS * ACOLS;   // 512, 256, 128
+  static constexpr int NA = K == 5 ? 2 : 4;           // A buffers (64 / 32 / 16 KB each)
+  static constexpr int H = D / 2;                     // members per producer / epilogue thread
+  static constexpr int NTH = 17 * 32;
+  static constexpr uint32_t AHSZ = 128u * KR * 4;     // one tf32 operand (hi or lo)
+  static constexpr uint32_t ASZT = 2 * AHSZ;          // bytes per A buffer
+  static constexpr uint32_t BHSZ = (uint32_t)KR * KR * 4;
+  static constexpr size_t SMEM = (size_t)NA * ASZT + 2 * (size_t)BHSZ;
+};
+
+template <int K>
+__global__ void __launch_bounds__(TcWsCfg<K>::NTH, 1)
+k_fused_tc_ws(float2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC64<K> U, int spin) {
+  using C = TcWsCfg<K>;
+  constexpr int D = C::D, KR = C::KR, H = C::H, NA = C::NA, NTS = C::NTS;
+  constexpr uint32_t SBO = (KR / 4) * 128;
+  extern __shared__ __align__(1024) unsigned char smem_tw[];
+  unsigned char* sA = smem_tw;                        // [buffer][hi, lo][128 x KR] tf32
+  unsigned char* sBh = sA + NA * C::ASZT;             // [KR x KR] tf32 (row n = output n), then lo
+  unsigned char* sBl = sBh + C::BHSZ;
+  __shared__ __align__(8) uint64_t bar_af[NA], bar_ae[NA], bar_tf[NTS], bar_te[NTS];
+  __shared__ __align__(8) uint64_t bar_drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+  __shared__ uint64_t s_moff[D];
+  __shared__ uint64_t s_pmoff[2][H + 1];          // producers' copy, rows apart by an odd word pair
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  auto sh_addr = [](const void* p) { return (uint32_t)__cvta_generic_to_shared(p); };
+  // B = R^T in K-major form is R row by row: B[n][k] = R[n][k], R = [[Ur, -Ui], [Ui, Ur]]
+  for (int i = t; i < KR * KR; i += C::NTH) {
+    const int n = i / KR, k = i % KR;
+    const float2 u = U.u[(n % D) * D + (k % D)];
+    const float v = n < D ? (k < D ? u.x : -u.y) : (k < D ? u.y : u.x);
+    const uint32_t hi = tf32_rna(v);
+    *reinterpret_cast<uint32_t*>(sBh + kmaj_off(n, k, KR)) = hi;
+    *reinterpret_cast<uint32_t*>(sBl + kmaj_off(n, k, KR)) = tf32_rna(v - __uint_as_float(hi));
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (t < D) s_moff[t] = s_pmoff[t / H][t % H] = g.hoff[g.run_of[t]] + g.loff[t];
+  if (t == 0) {
+    s_abort = 0;
+    auto init = [](uint64_t* b, uint32_t count) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"((uint32_t)__cvta_generic_to_shared(b)), "r"(count)
+                   : "memory");
+    };
+    for (int a = 0; a < NA; a++) { init(&bar_af[a], 256); init(&bar_ae[a], 1); }
+    for (int j = 0; j < NTS; j++) { init(&bar_tf[j], 1); init(&bar_te[j], 256); }
+    init(&bar_drain, 1);
+  }
+  if (w == 16) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(sh_addr(&tmem_slot)),
+                 "r"(C::NCOL) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t L = 1u << g.lb;
+  auto tile_base = [&](uint64_t T) {
+    uint64_t b = T << g.tg_log;
+    for (int i = 0; i < g.nins; i++) b = qc_insert_zero(b, g.ins[i]);
+    return (b | g.orval) & ~(uint64_t)(L - 1);
+  };
+
+  if (w < 8) {
+    // ------------------------------------------------ producers
+    const int row = t >> 1, m0 = (t & 1) * H;
+    const uint64_t goff = g.goff[row];
+    // this tile's members; the next tile's are loaded once these are in the A buffer
+    float2 x[H];
+    uint64_t T = blockIdx.x;
+    if (T < g.ntiles) {
+      const uint64_t base = tile_base(T) + goff;
+#pragma unroll
+      for (int r = 0; r < H; r++) x[r] = st[base + s_pmoff[t & 1][r]];
+    }
+    for (int i = 0; T < g.ntiles; i++, T += gridDim.x) {
+      const int a = i % NA;
+      if (i >= NA && !ws_wait(sh_addr(&bar_ae[a]), (uint32_t)((i / NA - 1) & 1), spin, &s_abort)) break;
+      unsigned char* sAh = sA + a * C::ASZT;
+      unsigned char* sAl = sAh + C::AHSZ;
+      // Re -> column m0 + r, Im -> column D + m0 + r
+#pragma unroll
+      for (int comp = 0; comp < 2; comp++) {
+#pragma unroll
+        for (int c4 = 0; c4 < H; c4 += 4) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            const float v = comp == 0 ? x[c4 + j].x : x[c4 + j].y;
+            hi[j] = tf32_rna(v);
+            lo[j] = tf32_rna(v - __uint_as_float(hi[j]));
+          }
+          const int col = comp * D + m0 + c4;
+          *reinterpret_cast<uint4*>(sAh + kmaj_off(row, col, KR)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(sAl + kmaj_off(row, col, KR)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      ws_arrive(sh_addr(&bar_af[a]));
+      const uint64_t Tn = T + gridDim.x;
+      if (Tn < g.ntiles) {
+        const uint64_t base = tile_base(Tn) + goff;
+#pragma unroll
+        for (int r = 0; r < H; r++) x[r] = st[base + s_pmoff[t & 1][r]];
+      }
+    }
+  } else if (w < 16) {
+    // ------------------------------------------------ epilogue: columns m = Re, D + m = Im (hi*hi), KR + ... (cross)
+    const int q = w & 3, m0 = ((w - 8) >> 2) * H;
+    const int row = 32 * q + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+    const uint64_t goff = g.goff[row];
+    uint64_t T = blockIdx.x;
+    for (int i = 0; T < g.ntiles; i++, T += gridDim.x) {
+      const int slot = i % NTS;
+      if (!ws_wait(sh_addr(&bar_tf[slot]), (uint32_t)((i / NTS) & 1), spin, &s_abort)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t obase = tile_base(T) + goff;
+      const uint32_t sbase = lane_base + (uint32_t)(slot * C::ACOLS + m0);
+      constexpr int NC = H < 16 ? H : 16;
+#pragma unroll
+      for (int c = 0; c < H; c += NC) {
+        uint32_t re0[NC], im0[NC], re1[NC], im1[NC];
+        tmem_ld<NC>(sbase + (uint32_t)c, re0);
+        tmem_ld<NC>(sbase + (uint32_t)(D + c), im0);
+        tmem_ld<NC>(sbase + (uint32_t)(KR + c), re1);
+        tmem_ld<NC>(sbase + (uint32_t)(KR + D + c), im1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (c + NC >= H) {
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          ws_arrive(sh_addr(&bar_te[slot]));
+        }
+#pragma unroll
+        for (int j = 0; j < NC; j++)
+          st[obase + s_moff[m0 + c + j]] = make_float2(__uint_as_float(re0[j]) + __uint_as_float(re1[j]),
+                                                       __uint_as_float(im0[j]) + __uint_as_float(im1[j]));
+      }
+    }
+  } else {
+    // ------------------------------------------------ MMA warp: Ah x [Bh; Bl] (N = 2 KR), then Al x Bh into [KR, 2 KR)
+    uint32_t lead;
+    asm volatile("{ .reg .pred p; elect.sync _|p, 0xffffffff; selp.u32 %0, 1, 0, p; }" : "=r"(lead));
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(KR >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const uint32_t idesc2 =
+        (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)((2 * KR) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const uint64_t adesc0 = umma_desc(sh_addr(sA), 128, SBO), bdesc0 = umma_desc(sh_addr(sBh), 128, SBO);
+    const uint32_t alo0 = (uint32_t)adesc0, ahi = (uint32_t)(adesc0 >> 32);
+    const uint32_t blo0 = (uint32_t)bdesc0, bhi = (uint32_t)(bdesc0 >> 32);
+    bool go = true;
+    uint64_t T = blockIdx.x;
+    for (int i = 0; go && T < g.ntiles; i++, T += gridDim.x) {
+      const int a = i % NA, slot = i % NTS;
+      if (!ws_wait(sh_addr(&bar_af[a]), (uint32_t)((i / NA) & 1), spin, &s_abort)) break;
+      if (i >= NTS && !ws_wait(sh_addr(&bar_te[slot]), (uint32_t)((i / NTS - 1) & 1), spin, &s_abort)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int p = 0; p < 2; p++) {
+        const uint32_t d = tmem + (uint32_t)(slot * C::ACOLS + (p == 0 ? 0 : KR));
+        const uint32_t alo = alo0 + (uint32_t)((a * C::ASZT + (p == 1 ? C::AHSZ : 0u)) >> 4);
+        const uint32_t id = p == 0 ? idesc2 : idesc;
+#pragma unroll
+        for (int kk = 0; kk < KR / 8; kk++) {
+          const uint64_t ad = ((uint64_t)ahi << 32) | (alo + (uint32_t)(kk * 16));
+          const uint64_t bd = ((uint64_t)bhi << 32) | (blo0 + (uint32_t)(kk * 16));
+          asm volatile("{ .reg .pred q, e; setp.ne.b32 q, %4, 0; setp.ne.b32 e, %5, 0;\n"
+                       "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q; }"
+                       :: "r"(d), "l"(ad), "l"(bd), "r"(id), "r"((p == 1 || kk > 0) ? 1 : 0), "r"(lead) : "memory");
+        }
+      }
+      ws_commit(sh_addr(&bar_tf[slot]), lead);
+      ws_commit(sh_addr(&bar_ae[a]), lead);
+    }
+    ws_commit(sh_addr(&bar_drain), lead);
+    mbar_poll(sh_addr(&bar_drain), 0, kTcSpinDefault);
+    __syncwarp();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 16) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(C::NCOL) : "memory");
+  }
+}
+
 // ---------------------------------------------------------------- fused tiles, complex128, TMA-staged
 // The complex128 tensor-core block of k_fused_tc128 with its input tiles
 // staged by the Tensor Memory Accelerator.  A block without controls below
@@ -1985,10 +2485,29 @@ int tc_spin(const qc_state* s) {
 }
 
 template <int K>
+int launch_fused_tc_ws_t(qc_state* s, const GeomF& g, const MatC64<K>& U) {
+  using C = TcWsCfg<K>;
+  static bool attr_set[64] = {};   // per device (function attributes are per device)
+  const int sdev = s->device;
+  if (sdev < 0 || sdev >= 64 || !attr_set[sdev]) {
+    QC_CUDA(cudaFuncSetAttribute(k_fused_tc_ws<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    QC_CUDA(cudaFuncSetAttribute(k_fused_tc_ws<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    if (sdev >= 0 && sdev < 64) attr_set[sdev] = true;
+  }
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, (uint64_t)qc_num_sms()));
+  k_fused_tc_ws<K><<<grid, C::NTH, C::SMEM, s->stream>>>((float2*)s->ptr, g, U, tc_spin(s));
+  QC_LAUNCHED("k_fused_tc_ws");
+  return QC_OK;
+}
+
+template <int K>
 int launch_fused_tc_t(qc_state* s, const qc_op& op, const GeomF& g) {
   constexpr int D = 1 << K, KR = 2 * D;
   MatC64<K> U;
   for (int i = 0; i < D * D; i++) U.u[i] = make_float2((float)op.U[2 * i], (float)op.U[2 * i + 1]);
+  // the warp-specialised pipeline only in mode 3 (the one-role kernel, two CTAs per SM, measured faster)
+  if (s->fused_tc == 3) return launch_fused_tc_ws_t<K>(s, g, U);
   const size_t smem = (size_t)2 * 128 * KR * 4 + (size_t)2 * KR * KR * 4;
   static int per_sm_dev[64] = {};   // per device (function attributes are per device)
   const int sdev = s->device;
@@ -2026,6 +2545,24 @@ template <int K>
 int launch_fused_tc128_tma_t(qc_state* s, const qc_op& op, const GeomF& g, int eu, int sh, const MatC128<K>& U);
 
 template <int K>
+int launch_fused_tc128_ws_t(qc_state* s, const GeomF& g, int eu, int sh, const MatC128<K>& U) {
+  using C = Tc128WsCfg<K>;
+  static bool attr_set[64] = {};   // per device (function attributes are per device)
+  const int sdev = s->device;
+  if (sdev < 0 || sdev >= 64 || !attr_set[sdev]) {
+    QC_CUDA(cudaFuncSetAttribute(k_fused_tc128_ws<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    QC_CUDA(cudaFuncSetAttribute(k_fused_tc128_ws<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    if (sdev >= 0 && sdev < 64) attr_set[sdev] = true;
+  }
+  // one CTA per SM: it holds all 512 tensor-memory columns
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(g.ntiles, (uint64_t)qc_num_sms()));
+  k_fused_tc128_ws<K><<<grid, C::NTH, C::SMEM, s->stream>>>((double2*)s->ptr, g, U, eu, sh, tc_spin(s));
+  QC_LAUNCHED("k_fused_tc128_ws");
+  return QC_OK;
+}
+
+template <int K>
 int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
   constexpr int D = 1 << K, KR = 2 * D;
   MatC128<K> U;
@@ -2049,6 +2586,9 @@ int launch_fused_tc128_t(qc_state* s, const qc_op& op, const GeomF& g) {
   // TMA-staged tiles: the tile is exactly its 128 groups (no control below the run length)
   if (s->fused_tc == 2 && ((size_t)1 << g.lb << g.kh) == ((size_t)128 << K) && tensor_map_encoder())
     return launch_fused_tc128_tma_t<K>(s, op, g, eu, sh, U);
+  // the warp-specialised pipeline: mode 3 always, the default (1) for k >= 4 (k = 3: the one-role kernel, two
+  // CTAs per SM, measured faster)
+  if (s->fused_tc == 3 || (s->fused_tc == 1 && K >= 4)) return launch_fused_tc128_ws_t<K>(s, g, eu, sh, U);
   const size_t smem = (size_t)kTcA * 128 * KR * 2 + (size_t)kTcB * KR * KR * 2;
   static int per_sm_dev[64] = {};   // per device (function attributes are per device)
   const int sdev = s->device;

@@ -199,7 +199,7 @@ int qc_set_stream(qc_state* s, void* stream) {
 
 int qc_set_fused_tc(qc_state* s, int enable) {
   if (!s) return qc_fail(QC_ERR_ARG, "state handle is NULL");
-  if (enable < 0 || enable > 2) return qc_fail(QC_ERR_ARG, "qc_set_fused_tc: enable must be 0, 1 or 2");
+  if (enable < 0 || enable > 4) return qc_fail(QC_ERR_ARG, "qc_set_fused_tc: enable must be 0 .. 4");
   s->fused_tc = enable;
   return QC_OK;
 }

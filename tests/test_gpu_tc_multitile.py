@@ -9,9 +9,10 @@ so these cases exercise the second and later tiles of every CTA.  Each is
 compared element by element with the FP64 oracle (Eq. (1), Sec. 2.4) at the
 amplitude tolerances: 1e-12 (complex128), 2e-5 (complex64).
 
-The last test runs the wait-limit path: with a limit of zero polls every
-CTA's first MMA wait gives up, the kernel waits for the MMAs it committed
-before freeing its tensor memory, and the next synchronising call reports
+The wait-limit test runs the time-out path of both kernels (the one-role
+kernel and the warp-specialised pipeline): with a limit of zero polls the
+first wait gives up, the kernel waits for the MMAs it committed before
+freeing its tensor memory, and the next synchronising call reports
 QC_ERR_TIMEOUT; the context stays usable.
 """
 import numpy as np
@@ -85,8 +86,8 @@ def test_multitile_blocks_against_oracle(q, n, k, dtype):
     assert q.device_status()["tc_timeouts"] == 0
 
 
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_wait_limit_reports_timeout_and_recovers(q, dtype):
+@pytest.mark.parametrize("dtype,mode", [("c64", 1), ("c64", 3), ("c128", 3), ("c128", 4)])
+def test_wait_limit_reports_timeout_and_recovers(q, dtype, mode):
     dt = q.C128 if dtype == "c128" else q.C64
     n, k = 20, 5
     rng = np.random.default_rng(77 + dt)
@@ -95,6 +96,7 @@ def test_wait_limit_reports_timeout_and_recovers(q, dtype):
     st = q.State(n, dt)
     if dt == q.C128:
         st.set_arith(q.ARITH_F32X2)
+    st.set_fused_tc(mode)
     st.from_numpy(phi)
     st.set_wait_limit(-1)                      # every first MMA wait gives up at once
     st.apply_kq(g.matrix, g.qubits)
@@ -114,19 +116,25 @@ def test_wait_limit_reports_timeout_and_recovers(q, dtype):
     assert float(np.abs(got - ref).max()) <= (1e-12 if dt == q.C128 else 2e-5)
 
 
+@pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("k", [3, 4, 5])
-def test_tma_staged_tiles_equal_register_loads(q, k):
-    """complex128 blocks: tiles loaded by each thread (qc_set_fused_tc 1) and
-    staged by the Tensor Memory Accelerator (2) run the same arithmetic,
-    so the states agree bit for bit; both match the oracle.  Placements: low,
-    high and spread targets (TMA-staged in mode 2), and a control below the
-    run length (per-thread loads in both modes)."""
+def test_kernel_variants_equal_register_loads(q, k, mode):
+    """complex128 blocks: the one-role kernel with per-thread loads
+    (qc_set_fused_tc 4), the same with tiles staged by the Tensor Memory
+    Accelerator (2), the warp-specialised pipeline (3) and the default
+    choice between them (1) run the same arithmetic, so the states agree bit
+    for bit; all match the oracle.
+    Placements: low, high and spread targets (TMA-staged in mode 2), and a
+    control below the run length (per-thread loads in mode 2).  At n = 22 a
+    CTA of the pipeline runs up to 2^15 / 152 tiles, so its A-buffer,
+    accumulator-slot and row-scale rings all wrap many times."""
     n = 22
     rng = np.random.default_rng(500 + k)
     gates = placements(rng, n, k)
     phi = C.random_state(n, 501)
+    phi[: 1 << 10] *= 30.0
     outs = []
-    for mode in (1, 2):
+    for mode in (4, mode):
         st = q.State(n, q.C128)
         st.set_arith(q.ARITH_F32X2)
         st.set_fused_tc(mode)
@@ -138,3 +146,30 @@ def test_tma_staged_tiles_equal_register_loads(q, k):
     np.testing.assert_array_equal(outs[0], outs[1])
     ref = O.run_circuit(n, gates, phi)
     assert float(np.abs(outs[0] - ref).max()) <= 1e-12
+    assert q.device_status()["tc_timeouts"] == 0
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_c64_pipeline_equals_one_role_kernel(q, k):
+    """complex64 blocks: the warp-specialised pipeline (qc_set_fused_tc 3)
+    computes the same split-TF32 products into the same accumulators as the
+    one-role kernel (4), so the states agree bit for bit; both match the
+    oracle.  n = 22: every CTA runs many tiles, so the A-buffer and
+    accumulator-slot rings wrap many times."""
+    n = 22
+    rng = np.random.default_rng(700 + k)
+    gates = placements(rng, n, k)
+    phi = C.random_state(n, 701).astype(np.complex64)
+    outs = []
+    for mode in (4, 3):
+        st = q.State(n, q.C64)
+        st.set_fused_tc(mode)
+        st.from_numpy(phi)
+        for g in gates:
+            st.apply_kq(g.matrix, g.qubits, g.controls, g.cstates)
+        outs.append(st.to_numpy())
+        st.free()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    ref = O.run_circuit(n, gates, phi.astype(np.complex128))
+    assert float(np.abs(outs[1].astype(np.complex128) - ref).max()) <= 2e-5
+    assert q.device_status()["tc_timeouts"] == 0
