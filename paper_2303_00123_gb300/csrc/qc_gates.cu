@@ -1074,6 +1074,19 @@ k_fused_tc128(double2* __restrict__ st, const __grid_constant__ GeomF g, const _
 // tensor memory is freed the MMA warp waits for the MMAs it committed.
 constexpr int kTcFlushScale = -0x7fffffff - 1;   // row scale of a group whose outputs are zero
 
+// Asynchronous 16- and 8-byte global -> shared copies (one thread's own
+// staging slots; it waits for its own copies before reading them).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int K> struct Tc128WsCfg {
   static constexpr int D = 1 << K, KR = 2 * D;
   static constexpr int NP = K == 5 ? 2 : 1;           // accumulator parts per tile
@@ -1089,7 +1102,8 @@ template <int K> struct Tc128WsCfg {
   static constexpr uint32_t ASZ = 128u * KR * 2;      // bytes per state digit slice
   static constexpr uint32_t ASZT = kTcA * ASZ;        // bytes per A buffer
   static constexpr uint32_t BPZ = kTcB * PC * KR * 2; // bytes of matrix digits per part
-  static constexpr size_t SMEM = (size_t)NA * ASZT + (size_t)NP * BPZ;
+  static constexpr uint32_t XSZ = 256u * H * 16;      // staging of the next tile: [member][producer] double2
+  static constexpr size_t SMEM = (size_t)NA * ASZT + (size_t)NP * BPZ + XSZ;
 };
 
 // Poll an mbarrier phase for up to `limit` tries, giving up early when the
@@ -1188,21 +1202,34 @@ k_fused_tc128_ws(double2* __restrict__ st, const __grid_constant__ GeomF g, cons
     // ------------------------------------------------ producers
     const int row = t >> 1, m0 = (t & 1) * H;
     const uint64_t goff = g.goff[row];
-    // this tile's members; the next tile's are loaded once these are in the A buffer
+    // A tile's members arrive by asynchronous copies into this thread's staging
+    // slots ([member][thread]: a warp's reads of one member are consecutive); the
+    // next tile's copies start as soon as this tile's members are in registers, so
+    // their latency overlaps the whole tile.
+    double2* sX = reinterpret_cast<double2*>(sB + NP * C::BPZ);
+    auto stage = [&](uint64_t Tn) {
+      const uint64_t base = tile_base(Tn) + goff;
+#pragma unroll
+      for (int r = 0; r < H; r++) cp_async16(sX + r * 256 + t, st + base + s_pmoff[t & 1][r]);
+      cp_async_commit();
+    };
     double2 x[H];
     uint64_t T = blockIdx.x;
-    if (T < g.ntiles) {
-      const uint64_t base = tile_base(T) + goff;
-#pragma unroll
-      for (int r = 0; r < H; r++) x[r] = st[base + s_pmoff[t & 1][r]];
-    }
+    if (T < g.ntiles) stage(T);
     for (int i = 0; T < g.ntiles; i++, T += gridDim.x) {
+      cp_async_wait_all();
+#pragma unroll
+      for (int r = 0; r < H; r++) x[r] = sX[r * 256 + t];
       int em = 0;
 #pragma unroll
       for (int r = 0; r < H; r++) {
         em = max(em, (__double2hiint(x[r].x) >> 20) & 0x7FF);
         em = max(em, (__double2hiint(x[r].y) >> 20) & 0x7FF);
       }
+      // em is computed from every slot's value, so the slot reads have completed before the
+      // (in-order issued) copies of the next tile may overwrite them
+      asm volatile("" :: "r"(em) : "memory");
+      if (T + gridDim.x < g.ntiles) stage(T + gridDim.x);
       em = max(em, __shfl_xor_sync(0xffffffffu, em, 1));
       const int a = i % NA;
       if (i >= NA && !ws_wait(sh_addr(&bar_ae[a]), (uint32_t)((i / NA - 1) & 1), spin, &s_abort)) break;
@@ -1240,13 +1267,8 @@ k_fused_tc128_ws(double2* __restrict__ st, const __grid_constant__ GeomF g, cons
       if (i >= NMS && !ws_wait(sh_addr(&bar_me[ms]), (uint32_t)((i / NMS - 1) & 1), spin, &s_abort)) break;
       if ((t & 1) == 0) s_scale[ms][row] = em + eu < 64 ? kTcFlushScale : em - 1077 + eu + sh;
       ws_arrive(sh_addr(&bar_mf[ms]));
-      const uint64_t Tn = T + gridDim.x;
-      if (Tn < g.ntiles) {
-        const uint64_t base = tile_base(Tn) + goff;
-#pragma unroll
-        for (int r = 0; r < H; r++) x[r] = st[base + s_pmoff[t & 1][r]];
-      }
     }
+    cp_async_wait_all();
   } else if (w < 16) {
     // ------------------------------------------------ epilogue
     const int q = w & 3, ep = (w - 8) >> 2;
@@ -1369,7 +1391,8 @@ template <int K> struct TcWsCfg {
   static constexpr uint32_t AHSZ = 128u * KR * 4;     // one tf32 operand (hi or lo)
   static constexpr uint32_t ASZT = 2 * AHSZ;          // bytes per A buffer
   static constexpr uint32_t BHSZ = (uint32_t)KR * KR * 4;
-  static constexpr size_t SMEM = (size_t)NA * ASZT + 2 * (size_t)BHSZ;
+  static constexpr uint32_t XSZ = 256u * H * 8;       // staging of the next tile: [member][producer] float2
+  static constexpr size_t SMEM = (size_t)NA * ASZT + 2 * (size_t)BHSZ + XSZ;
 };
 
 template <int K>
@@ -1432,15 +1455,28 @@ k_fused_tc_ws(float2* __restrict__ st, const __grid_constant__ GeomF g, const __
     // ------------------------------------------------ producers
     const int row = t >> 1, m0 = (t & 1) * H;
     const uint64_t goff = g.goff[row];
-    // this tile's members; the next tile's are loaded once these are in the A buffer
+    // staged tiles as in k_fused_tc128_ws ([member][thread] float2 slots)
+    float2* sX = reinterpret_cast<float2*>(sBl + C::BHSZ);
+    auto stage = [&](uint64_t Tn) {
+      const uint64_t base = tile_base(Tn) + goff;
+#pragma unroll
+      for (int r = 0; r < H; r++) cp_async8(sX + r * 256 + t, st + base + s_pmoff[t & 1][r]);
+      cp_async_commit();
+    };
     float2 x[H];
     uint64_t T = blockIdx.x;
-    if (T < g.ntiles) {
-      const uint64_t base = tile_base(T) + goff;
-#pragma unroll
-      for (int r = 0; r < H; r++) x[r] = st[base + s_pmoff[t & 1][r]];
-    }
+    if (T < g.ntiles) stage(T);
     for (int i = 0; T < g.ntiles; i++, T += gridDim.x) {
+      cp_async_wait_all();
+#pragma unroll
+      for (int r = 0; r < H; r++) x[r] = sX[r * 256 + t];
+      // a value computed from every slot's value: the slot reads have completed before the
+      // (in-order issued) copies of the next tile may overwrite them
+      uint32_t tok = 0;
+#pragma unroll
+      for (int r = 0; r < H; r++) tok |= __float_as_uint(x[r].x) ^ __float_as_uint(x[r].y);
+      asm volatile("" :: "r"(tok) : "memory");
+      if (T + gridDim.x < g.ntiles) stage(T + gridDim.x);
       const int a = i % NA;
       if (i >= NA && !ws_wait(sh_addr(&bar_ae[a]), (uint32_t)((i / NA - 1) & 1), spin, &s_abort)) break;
       unsigned char* sAh = sA + a * C::ASZT;
@@ -1464,13 +1500,8 @@ k_fused_tc_ws(float2* __restrict__ st, const __grid_constant__ GeomF g, const __
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       ws_arrive(sh_addr(&bar_af[a]));
-      const uint64_t Tn = T + gridDim.x;
-      if (Tn < g.ntiles) {
-        const uint64_t base = tile_base(Tn) + goff;
-#pragma unroll
-        for (int r = 0; r < H; r++) x[r] = st[base + s_pmoff[t & 1][r]];
-      }
     }
+    cp_async_wait_all();
   } else if (w < 16) {
     // ------------------------------------------------ epilogue: columns m = Re, D + m = Im (hi*hi), KR + ... (cross)
     const int q = w & 3, m0 = ((w - 8) >> 2) * H;
