@@ -1096,6 +1096,7 @@ template <int K> struct Tc128WsCfg {
   static constexpr int NTS = 512 / PCOLS;             // accumulator slots (k = 5, 4: 2; k = 3: 4)
   static constexpr int NA = K == 5 ? 1 : (K == 4 ? 3 : 4);   // A buffers (96 / 48 / 24 KB each)
   static constexpr int NMS = 4;                       // row-scale slots
+  static constexpr int NSTG = KR >= 32 ? 2 : 1;       // A-buffer stages (Re columns, Im columns)
   static constexpr int H = D / 2;                     // members per producer thread
   static constexpr int EM = PM / 2;                   // members per epilogue thread and part
   static constexpr int NTH = 17 * 32;                 // 8 producer + 8 epilogue warps + the MMA warp
@@ -1145,7 +1146,9 @@ k_fused_tc128_ws(double2* __restrict__ st, const __grid_constant__ GeomF g, cons
   extern __shared__ __align__(1024) unsigned char smem_ws[];
   unsigned char* sA = smem_ws;                        // [buffer][digit][128 x KR] fp16
   unsigned char* sB = sA + NA * C::ASZT;              // [part][digit][PC rows x KR] fp16
-  __shared__ __align__(8) uint64_t bar_af[NA], bar_ae[NA], bar_tf[NTS], bar_te[NTS], bar_mf[NMS], bar_me[NMS];
+  // A buffers in NSTG stages (k >= 4: the Re columns, then the Im columns of every member)
+  constexpr int NSTG = C::NSTG, KPS = (KR / 16) / NSTG;   // K steps of 16 columns per stage
+  __shared__ __align__(8) uint64_t bar_af[NA][NSTG], bar_ae[NA][NSTG], bar_tf[NTS], bar_te[NTS], bar_mf[NMS], bar_me[NMS];
   __shared__ __align__(8) uint64_t bar_drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
@@ -1176,7 +1179,8 @@ k_fused_tc128_ws(double2* __restrict__ st, const __grid_constant__ GeomF g, cons
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"((uint32_t)__cvta_generic_to_shared(b)), "r"(count)
                    : "memory");
     };
-    for (int a = 0; a < NA; a++) { init(&bar_af[a], 256); init(&bar_ae[a], 1); }
+    for (int a = 0; a < NA; a++)
+      for (int z = 0; z < NSTG; z++) { init(&bar_af[a][z], 256); init(&bar_ae[a][z], 1); }
     for (int j = 0; j < NTS; j++) { init(&bar_tf[j], 1); init(&bar_te[j], 256); }
     for (int j = 0; j < NMS; j++) { init(&bar_mf[j], 256); init(&bar_me[j], 256); }
     init(&bar_drain, 1);
@@ -1232,11 +1236,18 @@ k_fused_tc128_ws(double2* __restrict__ st, const __grid_constant__ GeomF g, cons
       if (T + gridDim.x < g.ntiles) stage(T + gridDim.x);
       em = max(em, __shfl_xor_sync(0xffffffffu, em, 1));
       const int a = i % NA;
-      if (i >= NA && !ws_wait(sh_addr(&bar_ae[a]), (uint32_t)((i / NA - 1) & 1), spin, &s_abort)) break;
       unsigned char* sAa = sA + a * C::ASZT;
-      // Re -> column m0 + r, Im -> column D + m0 + r; 16-byte stores (8 columns) where the thread has them
+      // Re -> column m0 + r, Im -> column D + m0 + r; 16-byte stores (8 columns) where the thread has them.
+      // With two stages the Re columns are handed to the MMA warp before the Im columns are written.
+      bool ok = true;
 #pragma unroll
       for (int comp = 0; comp < 2; comp++) {
+        const int z = NSTG == 2 ? comp : 0;
+        if ((comp == 0 || NSTG == 2) && i >= NA &&
+            !ws_wait(sh_addr(&bar_ae[a][z]), (uint32_t)((i / NA - 1) & 1), spin, &s_abort)) {
+          ok = false;
+          break;
+        }
         constexpr int CW = H >= 8 ? 8 : 4;
 #pragma unroll
         for (int c0 = 0; c0 < H; c0 += CW) {
@@ -1259,9 +1270,12 @@ k_fused_tc128_ws(double2* __restrict__ st, const __grid_constant__ GeomF g, cons
               *reinterpret_cast<uint2*>(sAa + s * C::ASZ + kmaj16_off(row, col, KR)) = make_uint2(wd[0][s], wd[1][s]);
           }
         }
+        if (comp == 1 || NSTG == 2) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          ws_arrive(sh_addr(&bar_af[a][z]));
+        }
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      ws_arrive(sh_addr(&bar_af[a]));
+      if (!ok) break;
       // the row's output scale (value = sum * 2^(E - 1077 + eu), E the exponent field; groups below 2^-959 give zero)
       const int ms = i % NMS;
       if (i >= NMS && !ws_wait(sh_addr(&bar_me[ms]), (uint32_t)((i / NMS - 1) & 1), spin, &s_abort)) break;
@@ -1328,35 +1342,43 @@ k_fused_tc128_ws(double2* __restrict__ st, const __grid_constant__ GeomF g, cons
     uint64_t T = blockIdx.x;
     for (int i = 0; go && T < g.ntiles; i++, T += gridDim.x) {
       const int a = i % NA;
-      if (!ws_wait(sh_addr(&bar_af[a]), (uint32_t)((i / NA) & 1), spin, &s_abort)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-      for (int p = 0; p < NP; p++) {
+      for (int p = 0; p < NP && go; p++) {
         const int j = i * NP + p, slot = j % NTS;
         if (j >= NTS && !ws_wait(sh_addr(&bar_te[slot]), (uint32_t)((j / NTS - 1) & 1), spin, &s_abort)) {
           go = false;
           break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // state digit sa against matrix digits 0 .. 6 - sa: one MMA per K step, N = (7 - sa) PC,
-        // accumulator columns from level sa
 #pragma unroll
-        for (int sa = 0; sa < kTcA; sa++) {
-          const int nt = kTcLev - sa;
-          const uint32_t idn = (1u << 4) | ((uint32_t)((nt * PC) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-#pragma unroll
-          for (int kk = 0; kk < KR / 16; kk++) {
-            const uint64_t ad = ((uint64_t)ahi << 32) | (alo + (uint32_t)((a * C::ASZT + sa * C::ASZ + kk * 256) >> 4));
-            const uint64_t bd = ((uint64_t)bhi << 32) | (blo + (uint32_t)((p * C::BPZ + kk * 256) >> 4));
-            asm volatile("{ .reg .pred q, e; setp.ne.b32 q, %4, 0; setp.ne.b32 e, %5, 0;\n"
-                         "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q; }"
-                         :: "r"(tmem + (uint32_t)(slot * C::PCOLS + sa * PC)), "l"(ad), "l"(bd), "r"(idn),
-                            "r"((sa > 0 || kk > 0) ? 1 : 0), "r"(lead) : "memory");
+        for (int z = 0; z < NSTG; z++) {
+          // (part 1 finds the stage's phase already complete)
+          if (!ws_wait(sh_addr(&bar_af[a][z]), (uint32_t)((i / NA) & 1), spin, &s_abort)) {
+            go = false;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // state digit sa against matrix digits 0 .. 6 - sa: one MMA per K step, N = (7 - sa) PC,
+          // accumulator columns from level sa
+#pragma unroll
+          for (int sa = 0; sa < kTcA; sa++) {
+            const int nt = kTcLev - sa;
+            const uint32_t idn = (1u << 4) | ((uint32_t)((nt * PC) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+#pragma unroll
+            for (int k2 = 0; k2 < KPS; k2++) {
+              const int kk = z * KPS + k2;
+              const uint64_t ad = ((uint64_t)ahi << 32) | (alo + (uint32_t)((a * C::ASZT + sa * C::ASZ + kk * 256) >> 4));
+              const uint64_t bd = ((uint64_t)bhi << 32) | (blo + (uint32_t)((p * C::BPZ + kk * 256) >> 4));
+              asm volatile("{ .reg .pred q, e; setp.ne.b32 q, %4, 0; setp.ne.b32 e, %5, 0;\n"
+                           "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q; }"
+                           :: "r"(tmem + (uint32_t)(slot * C::PCOLS + sa * PC)), "l"(ad), "l"(bd), "r"(idn),
+                              "r"((sa > 0 || kk > 0) ? 1 : 0), "r"(lead) : "memory");
+            }
+          }
+          // the last part has read this stage of the A buffer: the producers may refill it
+          if (p == NP - 1) ws_commit(sh_addr(&bar_ae[a][z]), lead);
         }
-        ws_commit(sh_addr(&bar_tf[slot]), lead);
+        if (go) ws_commit(sh_addr(&bar_tf[slot]), lead);
       }
-      if (go) ws_commit(sh_addr(&bar_ae[a]), lead);
     }
     // every committed MMA has finished before the tensor memory is freed
     ws_commit(sh_addr(&bar_drain), lead);
