@@ -91,7 +91,11 @@ int qc_state_set_basis(qc_state* s, uint64_t x);
  * described at qc_device_status) or host -> device
  * (ordered on the state's stream; the host buffer must stay valid until the
  * stream reaches the copy when it is pinned, else the call is synchronous).
- * `host` holds 2^n interleaved (re, im) pairs of the state's element type. */
+ * `host` holds 2^n interleaved (re, im) pairs of the state's element type.
+ * Host -> device from page-locked host memory that CUDA has mapped
+ * (cudaHostRegister, cudaHostAlloc; 16-byte aligned) is done by a kernel
+ * reading the mapped memory, on the state's stream; from other memory by the
+ * copy engine. */
 int qc_state_copy_to_host(const qc_state* s, void* host);
 int qc_state_copy_from_host(qc_state* s, const void* host);
 

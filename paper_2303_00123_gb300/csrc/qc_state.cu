@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 
@@ -175,10 +176,30 @@ int qc_set_wait_limit(qc_state* s, long long polls) {
   return QC_OK;
 }
 
+// Host -> device copy by the GPU's own 16-byte loads from page-locked host
+// memory that CUDA has mapped into the device's address space.
+__global__ void k_copy_from_mapped(uint4* __restrict__ dst, const uint4* __restrict__ src, size_t n16) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
 int qc_state_copy_from_host(qc_state* s, const void* host) {
   if (int rc = qc_check_state(s)) return rc;
   if (!host) return qc_fail(QC_ERR_ARG, "host is NULL");
   const size_t bytes = ((size_t)1 << s->n) * elem_size(s->dtype);
+  // Page-locked, mapped host memory (cudaHostRegister, cudaHostAlloc): a copy kernel
+  // reading it (measured on GB300: 17 GB at 210 GB/s, where the copy engine gave
+  // 58-66 GB/s for the same registered buffer); anything else: the copy engine.
+  cudaPointerAttributes at;
+  const cudaError_t ae = cudaPointerGetAttributes(&at, host);
+  if (ae == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer &&
+      ((uintptr_t)at.devicePointer % 16) == 0 && ((uintptr_t)s->ptr % 16) == 0 && bytes % 16 == 0) {
+    k_copy_from_mapped<<<qc_num_sms() * 8, 512, 0, s->stream>>>((uint4*)s->ptr, (const uint4*)at.devicePointer,
+                                                              bytes / 16);
+    QC_LAUNCHED("k_copy_from_mapped");
+    return QC_OK;
+  }
+  if (ae != cudaSuccess) cudaGetLastError();
   QC_CUDA(cudaMemcpyAsync(s->ptr, host, bytes, cudaMemcpyHostToDevice, s->stream));
   return QC_OK;
 }
