@@ -384,9 +384,10 @@ typedef struct {
  * tile accumulated without rounding error in a fixed-exponent chain (the
  * rounding remainders and hi*lo cross terms in a second word), float-float
  * across a tile's terms, FP64 across tiles -- about 1e-15 from the exact value
- * for O(1) coefficients.  complex64: FP32 products and per-thread partial sums
- * of at most 16 products, float-float across tiles, FP64 block sums -- within
- * about 1e-6 * sum |c_t|.  QC_ERR_TIMEOUT as described at qc_device_status.
+ * for O(1) coefficients.  complex64: the same arithmetic on the FP32
+ * amplitudes as they are (their products are exact in two floats), so the
+ * result is the expectation of the complex64 state to about 1e-13 * sum |c_t|.
+ * QC_ERR_TIMEOUT as described at qc_device_status.
  * Deterministic (fixed grid, fixed reduction order). */
 int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out);
 

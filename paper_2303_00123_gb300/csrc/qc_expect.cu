@@ -342,24 +342,15 @@ __device__ __forceinline__ void tile_group(const unsigned char* tile, const TPas
       // w = conj(b) a:  Re w = br ar + bi ai (x + y of b*a),  Im w = br ai - bi ar
       // (x - y of b * swap(a)).  Products: hi*hi exact, cross terms rounded.
       const uint64_t ah_ = IM ? P2::swp(a[u].h) : a[u].h;
-      uint64_t p = 0, e = 0;
+      // hi*hi products exact (the FMA remainder e), complex128's cross terms rounded;
+      // complex64 amplitudes are their hi pairs (lo zero), so its products are exact
+      const uint64_t p = prod2(b[u].h, ah_, zz);
+      uint64_t e = P2::fma2(b[u].h, ah_, neg2(p));
       if constexpr (C128) {
-        p = prod2(b[u].h, ah_, zz);
-        e = P2::fma2(b[u].h, ah_, neg2(p));
         const uint64_t al_ = IM ? P2::swp(a[u].l) : a[u].l;
         e = P2::add2(e, P2::fma2(b[u].h, al_, P2::mul2(b[u].l, ah_)));
       }
-      if constexpr (!C128) {
-        // complex64: FP32 products and in-tile partial sums (one packed fma per
-        // pair and term); the sums across tiles stay float-float
-        if constexpr (SIGNED) {
-#pragma unroll
-          for (int k = 0; k < NA; k++)
-            if (k < g.nt) ah[k] = P2::fma2(P2::mul2(b[u].h, sgn2(__popc(l[u] & ql[k]))), ah_, ah[k]);
-        } else {
-          ah[0] = P2::fma2(b[u].h, ah_, ah[0]);
-        }
-      } else if constexpr (SIGNED) {
+      if constexpr (SIGNED) {
 #pragma unroll
         for (int k = 0; k < NA; k++) {
           if (k < g.nt) {
@@ -413,17 +404,13 @@ __device__ __forceinline__ void tile_diag(unsigned char* tile, const uint64_t* g
       if (l < ntile) {
         const typename T::amp a = T::get(tile, l);
         const uint64_t p = prod2(a.h, a.h, zz);
-        if constexpr (C128) {
-          // |a|^2 = re^2 + im^2: hi*hi exact (TwoProduct), 2 hi*lo rounded
-          uint64_t e = P2::fma2(a.h, a.h, neg2(p));
-          e = P2::add2(e, P2::mul2(P2::add2(a.h, a.h), a.l));
-          float s, r;
-          two_sum(P2::lo32(p), P2::hi32(p), s, r);
-          ph[k] = s;
-          pl[k] = __fadd_rn(r, __fadd_rn(P2::lo32(e), P2::hi32(e)));
-        } else {
-          ph[k] = __fadd_rn(P2::lo32(p), P2::hi32(p));     // complex64: FP32
-        }
+        // |a|^2 = re^2 + im^2: hi*hi exact (TwoProduct), complex128's 2 hi*lo rounded
+        uint64_t e = P2::fma2(a.h, a.h, neg2(p));
+        if constexpr (C128) e = P2::add2(e, P2::mul2(P2::add2(a.h, a.h), a.l));
+        float s, r;
+        two_sum(P2::lo32(p), P2::hi32(p), s, r);
+        ph[k] = s;
+        pl[k] = __fadd_rn(r, __fadd_rn(P2::lo32(e), P2::hi32(e)));
       }
     }
     // in-register Walsh-Hadamard transform over the 16 entries
@@ -433,18 +420,13 @@ __device__ __forceinline__ void tile_diag(unsigned char* tile, const uint64_t* g
       for (int k = 0; k < 16; k++) {
         if (!(k & b)) {
           const float xh = ph[k], xl = pl[k], yh = ph[k | b], yl = pl[k | b];
-          if constexpr (C128) {
-            float s, e;
-            two_sum(xh, yh, s, e);
-            ph[k] = s;
-            pl[k] = __fadd_rn(__fadd_rn(xl, yl), e);
-            two_sum(xh, -yh, s, e);
-            ph[k | b] = s;
-            pl[k | b] = __fadd_rn(__fsub_rn(xl, yl), e);
-          } else {
-            ph[k] = __fadd_rn(xh, yh);
-            ph[k | b] = __fsub_rn(xh, yh);
-          }
+          float s, e;
+          two_sum(xh, yh, s, e);
+          ph[k] = s;
+          pl[k] = __fadd_rn(__fadd_rn(xl, yl), e);
+          two_sum(xh, -yh, s, e);
+          ph[k | b] = s;
+          pl[k | b] = __fadd_rn(__fsub_rn(xl, yl), e);
         }
       }
     }
@@ -457,7 +439,6 @@ __device__ __forceinline__ void tile_diag(unsigned char* tile, const uint64_t* g
     // global index of the chunk's first entry: base ^ G(hc) ^ low
     const uint64_t y0 = base ^ gtab[start >> P.m] ^ (start & ((1u << P.m) - 1u));
     constexpr int TU = 4;          // terms per iteration, their loads issued first
-    float dsum = 0.f;              // complex64: the chunk's terms, summed in FP32
     for (int t0 = P.dt0; t0 < P.dt0 + P.dnt; t0 += TU) {
       uint32_t qlt[TU];
       uint64_t qt[TU];
@@ -481,19 +462,10 @@ __device__ __forceinline__ void tile_diag(unsigned char* tile, const uint64_t* g
         if (t0 + i < P.dt0 + P.dnt) {
           // sign (-1)^popc(y0 & Q) of the chunk's first index y0, folded into the weight
           const uint32_t sb = (uint32_t)__popcll(y0 & qt[i]) << 31;
-          if constexpr (C128)
-            acc_scaled(th, tl, __uint_as_float(__float_as_uint(kh[i]) ^ sb),
-                       __uint_as_float(__float_as_uint(kl[i]) ^ sb), w[i].x, w[i].y);
-          else
-            dsum = __fmaf_rn(__uint_as_float(__float_as_uint(kh[i]) ^ sb), w[i].x, dsum);
+          acc_scaled(th, tl, __uint_as_float(__float_as_uint(kh[i]) ^ sb),
+                     __uint_as_float(__float_as_uint(kl[i]) ^ sb), w[i].x, w[i].y);
         }
       }
-    }
-    if constexpr (!C128) {           // the chunk's FP32 sum joins the float-float total
-      float s, e;
-      two_sum(th, dsum, s, e);
-      th = s;
-      tl = __fadd_rn(tl, e);
     }
   }
 }
@@ -596,7 +568,7 @@ __device__ __forceinline__ void reg_pairs(const uint64_t* ah, const uint64_t* al
 #pragma unroll
   for (int c = 0; c < 2; c++)
 #pragma unroll
-    for (int k = 0; k < NA; k++) { t[c][k] = C128 ? sig : 0ull; lo[c][k] = 0ull; }
+    for (int k = 0; k < NA; k++) { t[c][k] = sig; lo[c][k] = 0ull; }
   int npair = 0;
 #pragma unroll
   for (int r = 0; r < 16; r++) {
@@ -624,14 +596,18 @@ __device__ __forceinline__ void reg_pairs(const uint64_t* ah, const uint64_t* al
         t[ch][k] = t1;
         lo[ch][k] = P2::fma2(bl, ahp, P2::fma2(bh, alp, P2::add2(lo[ch][k], rr)));
       } else {
-        t[ch][k] = P2::fma2(bh, ahp, t[ch][k]);
+        // complex64: the same chain without lo parts (exact products, float-float sums)
+        const uint64_t t1 = P2::fma2(bh, ahp, t[ch][k]);
+        const uint64_t rr = P2::fma2(bh, ahp, P2::sub2(t[ch][k], t1));
+        t[ch][k] = t1;
+        lo[ch][k] = P2::add2(lo[ch][k], rr);
       }
     }
   }
 #pragma unroll
   for (int k = 0; k < NA; k++) {
     // (t0 - sigma) + (t1 - sigma): multiples of ulp(sigma) below 2^(E-2) each, so exact
-    const uint64_t hi = C128 ? P2::add2(P2::sub2(t[0][k], sig), P2::sub2(t[1][k], sig)) : P2::add2(t[0][k], t[1][k]);
+    const uint64_t hi = P2::add2(P2::sub2(t[0][k], sig), P2::sub2(t[1][k], sig));
     const uint64_t lok = P2::add2(lo[0][k], lo[1][k]);
     const float hx = P2::lo32(hi), lx = P2::lo32(lok);
     const float hy = IM ? -P2::hi32(hi) : P2::hi32(hi);
@@ -742,8 +718,11 @@ __device__ __forceinline__ float reg_max(const uint64_t* ah) {
   return m;
 }
 
+// CTAs per SM of k_pauli_reg (its register bound: 128 / 85 registers a thread)
+constexpr int reg_ctas_per_sm(bool c128) { return c128 ? 2 : 3; }
+
 template <bool C128>
-__global__ void __launch_bounds__(kTileThreads, C128 ? 2 : 4)
+__global__ void __launch_bounds__(kTileThreads, reg_ctas_per_sm(C128))
 k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass P, double* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char rsm[];
   constexpr uint32_t kChunks = C128 ? (1u << kRegL) : (1u << (kRegL - 1));   // 16-byte chunks per tile
@@ -793,17 +772,12 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
 #pragma unroll
       for (int k = 0; k < 16; k++) {
         const uint64_t p = prod2(ah[k], ah[k], zz);
-        if constexpr (C128) {
-          uint64_t e = P2::fma2(ah[k], ah[k], neg2(p));
-          e = P2::add2(e, P2::mul2(P2::add2(ah[k], ah[k]), al[k]));
-          float s2, r2;
-          two_sum(P2::lo32(p), P2::hi32(p), s2, r2);
-          ph[k] = s2;
-          pl[k] = __fadd_rn(r2, __fadd_rn(P2::lo32(e), P2::hi32(e)));
-        } else {
-          ph[k] = __fadd_rn(P2::lo32(p), P2::hi32(p));
-          pl[k] = 0.f;
-        }
+        uint64_t e = P2::fma2(ah[k], ah[k], neg2(p));          // hi*hi exact
+        if constexpr (C128) e = P2::add2(e, P2::mul2(P2::add2(ah[k], ah[k]), al[k]));
+        float s2, r2;
+        two_sum(P2::lo32(p), P2::hi32(p), s2, r2);
+        ph[k] = s2;
+        pl[k] = __fadd_rn(r2, __fadd_rn(P2::lo32(e), P2::hi32(e)));
       }
 #pragma unroll
       for (int b = 1; b < 16; b <<= 1) {
@@ -811,18 +785,13 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
         for (int k = 0; k < 16; k++) {
           if (!(k & b)) {
             const float xh = ph[k], xl = pl[k], yh = ph[k | b], yl = pl[k | b];
-            if constexpr (C128) {
-              float s2, e2;
-              two_sum(xh, yh, s2, e2);
-              ph[k] = s2;
-              pl[k] = __fadd_rn(__fadd_rn(xl, yl), e2);
-              two_sum(xh, -yh, s2, e2);
-              ph[k | b] = s2;
-              pl[k | b] = __fadd_rn(__fsub_rn(xl, yl), e2);
-            } else {
-              ph[k] = __fadd_rn(xh, yh);
-              ph[k | b] = __fsub_rn(xh, yh);
-            }
+            float s2, e2;
+            two_sum(xh, yh, s2, e2);
+            ph[k] = s2;
+            pl[k] = __fadd_rn(__fadd_rn(xl, yl), e2);
+            two_sum(xh, -yh, s2, e2);
+            ph[k | b] = s2;
+            pl[k | b] = __fadd_rn(__fsub_rn(xl, yl), e2);
           }
         }
       }
@@ -832,23 +801,13 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
 #pragma unroll
       for (int k = 0; k < 16; k++) *(float2*)(own + 8 * ((uint32_t)k ^ wsw)) = make_float2(ph[k], pl[k]);
       const uint64_t y0 = base ^ gtab[lb0 >> P.m] ^ (lb0 & lowm);
-      float dsum = 0.f;
       for (int ti = P.dt0; ti < P.dt0 + P.dnt; ti++) {
         const TTerm* tt = &P.terms[ti];
         const uint32_t u = __ldg(&tt->ql) & 15u;
         const float2 w = *(const float2*)(own + 8 * (u ^ wsw));
         const uint32_t sb = (uint32_t)__popcll(y0 & __ldg(&tt->q)) << 31;
-        if constexpr (C128)
-          acc_scaled(th, tl, __uint_as_float(__float_as_uint(__ldg(&tt->kh)) ^ sb),
-                     __uint_as_float(__float_as_uint(__ldg(&tt->kl)) ^ sb), w.x, w.y);
-        else
-          dsum = __fmaf_rn(__uint_as_float(__float_as_uint(__ldg(&tt->kh)) ^ sb), w.x, dsum);
-      }
-      if constexpr (!C128) {
-        float s2, e2;
-        two_sum(th, dsum, s2, e2);
-        th = s2;
-        tl = __fadd_rn(tl, e2);
+        acc_scaled(th, tl, __uint_as_float(__float_as_uint(__ldg(&tt->kh)) ^ sb),
+                   __uint_as_float(__float_as_uint(__ldg(&tt->kl)) ^ sb), w.x, w.y);
       }
     }
     const bool later = P.garr[3] > P.garr[1] || P.ngroups > P.garr[3];
@@ -1172,9 +1131,6 @@ int launch_reg(const qc_state* s, const TPass& P, double* partial, int grid) {
   QC_LAUNCHED("k_pauli_reg");
   return QC_OK;
 }
-
-// CTAs per SM the register-resident kernel runs with (its launch bounds)
-constexpr int reg_ctas_per_sm(bool c128) { return c128 ? 2 : 4; }
 
 template <bool C128>
 int launch_tile(const qc_state* s, const TPass& P, double* partial, int grid) {
