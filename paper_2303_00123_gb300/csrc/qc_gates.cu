@@ -549,8 +549,11 @@ __device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t* r) {
 
 constexpr int kThreadsTC = 256;   // two threads per accumulator row, each owns half of the members
 
+// CTAs per SM the kernel is compiled for: 2 at k = 5 (96 KB of operands each), 3 below
+template <int K> struct TcMinB { static constexpr int v = K == 5 ? 2 : 3; };
+
 template <int K>
-__global__ void __launch_bounds__(kThreadsTC, 2)
+__global__ void __launch_bounds__(kThreadsTC, TcMinB<K>::v)
 k_fused_tc(float2* __restrict__ st, const __grid_constant__ GeomF g, const __grid_constant__ MatC64<K> U, int spin) {
   constexpr int D = 1 << K;
   constexpr int H = D / 2;                        // members per thread
@@ -837,7 +840,8 @@ __device__ __forceinline__ uint32_t kmaj16_off(int row, int col, int KR) {
 template <int K> struct Tc128Cfg {
   static constexpr int TPR = 2;                   // threads per row (group)
   static constexpr int NT = 128 * TPR;
-  static constexpr int MINB = K <= 4 ? 2 : 1;     // CTAs per SM (k <= 4: 2 x 256 TMEM columns, 2 x 62 KB)
+  static constexpr int MINB = K <= 4 ? 2 : 1;     // CTAs per SM (k <= 4: 2 x 256 TMEM columns, 2 x 62 KB;
+                                                  // 3 at k = 3 spilled and measured slower)
 };
 
 template <int K>
