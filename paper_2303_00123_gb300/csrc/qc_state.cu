@@ -187,12 +187,12 @@ int qc_state_copy_from_host(qc_state* s, const void* host) {
   if (int rc = qc_check_state(s)) return rc;
   if (!host) return qc_fail(QC_ERR_ARG, "host is NULL");
   const size_t bytes = ((size_t)1 << s->n) * elem_size(s->dtype);
-  // Page-locked, mapped host memory (cudaHostRegister, cudaHostAlloc): a copy kernel
+  // Page-locked host memory mapped for the state's device (cudaHostRegister, cudaHostAlloc): a copy kernel
   // reading it (measured on GB300: 17 GB at 210 GB/s, where the copy engine gave
   // 58-66 GB/s for the same registered buffer); anything else: the copy engine.
   cudaPointerAttributes at;
   const cudaError_t ae = cudaPointerGetAttributes(&at, host);
-  if (ae == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer &&
+  if (ae == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer && at.device == s->device &&
       ((uintptr_t)at.devicePointer % 16) == 0 && ((uintptr_t)s->ptr % 16) == 0 && bytes % 16 == 0) {
     k_copy_from_mapped<<<qc_num_sms() * 8, 512, 0, s->stream>>>((uint4*)s->ptr, (const uint4*)at.devicePointer,
                                                               bytes / 16);
