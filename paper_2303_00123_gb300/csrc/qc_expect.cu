@@ -170,8 +170,11 @@ struct TTerm {                     // one term inside a pass
   uint64_t q;                      // phase mask Q (global bit positions)
   uint32_t ql;                     // local phase mask QL
   uint32_t pad;
-  float kh, kl;                    // weight (c_t, times +-2 for pair terms) as hi + lo
+  float kh, kh2, kl, kl2;          // weight k (c_t, times +-2 for pair terms) as hi kh + lo kl;
+                                   // (kh2, kl2) = +-(kh, kl): the weight of the second lane of a
+                                   // packed pair sum, negative when the term weighs Im w
 };
+static_assert(sizeof(TTerm) == 32, "terms are 32-byte records; the weights are one 16-byte load");
 struct TGroup {                    // pair terms sharing one local flip mask
   uint32_t fl;                     // FL
   int pivot;                       // highest set bit of FL
@@ -185,6 +188,8 @@ struct TPass {                     // kernel parameter: one pass
   uint64_t ntiles;                 // 2^(n - L)
   int m, h, L, wb;                 // low bits, generators, tile bits, WHT window
   int ngroups, dt0, dnt;           // pair groups; diagonal terms [dt0, dt0 + dnt)
+  int dtile;                       // the first dtile diagonal terms have QL = 0 (their sign is
+                                   // the tile's: the register-resident kernel sums them per tile)
   int piv[kTileMaxH];              // pivot bit of generator i, ascending in i
   uint64_t gen[kTileMaxH];         // generator masks
   int garr[4];                     // register-resident kernel: groups [garr[a], garr[a+1]) (a < 3;
@@ -556,10 +561,14 @@ __device__ __forceinline__ uint64_t chain_sigma(float mx) {
 // One group of pair terms over the 16 register amplitudes (register bits of
 // the current arrangement, the group's flip mask FLR in them).  lsign[k]: the
 // parity of the thread's fixed local bits & QL of term k; qlr[k]: QL restricted
-// to the register bits.  Results go to (vh, vl) per accumulator.
+// to the register bits.  Per accumulator k the result is the packed pair of
+// lane sums: vh[k] (exact, a multiple of ulp(sigma)) + vl[k] (remainders and
+// cross terms); lane x holds the sum of br ar (IM: br ai), lane y of bi ai
+// (IM: bi ar), so Re w = x + y and Im w = x - y -- the term's packed weight
+// (k, +-k) takes that sign.
 template <bool C128, int FLR, bool IM, bool SIGNED>
 __device__ __forceinline__ void reg_pairs(const uint64_t* ah, const uint64_t* al, uint64_t sig, const uint32_t* lsign,
-                                          const uint32_t* qlr, int nt, float* vh, float* vl) {
+                                          const uint32_t* qlr, int nt, uint64_t* vh, uint64_t* vl) {
   constexpr int NA = SIGNED ? kGroupTerms : 1;
   constexpr int PIV = FLR >= 8 ? 8 : (FLR >= 4 ? 4 : (FLR >= 2 ? 2 : 1));
   // two independent chains per accumulator (alternate pairs): twice the
@@ -607,21 +616,15 @@ __device__ __forceinline__ void reg_pairs(const uint64_t* ah, const uint64_t* al
 #pragma unroll
   for (int k = 0; k < NA; k++) {
     // (t0 - sigma) + (t1 - sigma): multiples of ulp(sigma) below 2^(E-2) each, so exact
-    const uint64_t hi = P2::add2(P2::sub2(t[0][k], sig), P2::sub2(t[1][k], sig));
-    const uint64_t lok = P2::add2(lo[0][k], lo[1][k]);
-    const float hx = P2::lo32(hi), lx = P2::lo32(lok);
-    const float hy = IM ? -P2::hi32(hi) : P2::hi32(hi);
-    const float ly = IM ? -P2::hi32(lok) : P2::hi32(lok);
-    float ve;
-    two_sum(hx, hy, vh[k], ve);
-    vl[k] = __fadd_rn(ve, __fadd_rn(lx, ly));
+    vh[k] = P2::add2(P2::sub2(t[0][k], sig), P2::sub2(t[1][k], sig));
+    vl[k] = P2::add2(lo[0][k], lo[1][k]);
   }
 }
 
 template <bool C128, int FLR>
 __device__ __forceinline__ void reg_pairs_kind(uint32_t kind, const uint64_t* ah, const uint64_t* al, uint64_t sig,
-                                               const uint32_t* lsign, const uint32_t* qlr, int nt, float* vh,
-                                               float* vl) {
+                                               const uint32_t* lsign, const uint32_t* qlr, int nt, uint64_t* vh,
+                                               uint64_t* vl) {
   switch (kind) {
     case 0: reg_pairs<C128, FLR, false, false>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
     case 1: reg_pairs<C128, FLR, true, false>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
@@ -630,12 +633,23 @@ __device__ __forceinline__ void reg_pairs_kind(uint32_t kind, const uint64_t* ah
   }
 }
 
+// Packed weighted accumulation, per lane: (TH, TL) += (wh + wl) * (xh + xl),
+// wh * xh exact (TwoProduct), the cross terms rounded once, the sum TwoSum.
+__device__ __forceinline__ void acc_w2(uint64_t& TH, uint64_t& TL, uint64_t wh, uint64_t wl, uint64_t xh, uint64_t xl,
+                                       uint64_t zz) {
+  const uint64_t p = prod2(wh, xh, zz);
+  const uint64_t e = P2::fma2(wh, xh, neg2(p));
+  acc2(TH, TL, p, P2::fma2(wh, xl, P2::fma2(wl, xh, e)));
+}
+
 // The groups [g0, g1) of arrangement `a` (register bits [4a, 4a + 4)) for this
 // thread's registers; lbase = the thread's local index with zero register bits.
+// Each term adds its packed weight times the group's packed lane sums to the
+// packed accumulator (TH, TL); the lanes are added once per tile.
 template <bool C128>
 __device__ __forceinline__ void reg_groups(const TPass& P, int g0, int g1, int a, uint32_t lbase, uint64_t base,
-                                           const uint64_t* ah, const uint64_t* al, uint64_t sig, float& th,
-                                           float& tl) {
+                                           const uint64_t* ah, const uint64_t* al, uint64_t sig, uint64_t zz,
+                                           uint64_t& TH, uint64_t& TL) {
   for (int gi = g0; gi < g1; gi++) {
     const uint32_t fl = __ldg(&P.groups[gi].fl);
     const int t0 = __ldg(&P.groups[gi].t0);
@@ -653,7 +667,7 @@ __device__ __forceinline__ void reg_groups(const TPass& P, int g0, int g1, int a
         qlr[1] = (q1 >> (4 * a)) & 15u;
       }
     }
-    float vh[kGroupTerms] = {0.f, 0.f}, vl[kGroupTerms] = {0.f, 0.f};
+    uint64_t vh[kGroupTerms] = {0ull, 0ull}, vl[kGroupTerms] = {0ull, 0ull};
     switch ((fl >> (4 * a)) & 15u) {
 #define QC_REG_CASE(F) case F: reg_pairs_kind<C128, F>(kind, ah, al, sig, lsign, qlr, nt, vh, vl); break;
       QC_REG_CASE(1) QC_REG_CASE(2) QC_REG_CASE(3) QC_REG_CASE(4) QC_REG_CASE(5) QC_REG_CASE(6) QC_REG_CASE(7)
@@ -665,12 +679,36 @@ __device__ __forceinline__ void reg_groups(const TPass& P, int g0, int g1, int a
     const bool signed_ = (kind & 2u) != 0;
     for (int k = 0; k < nt; k++) {
       const TTerm* tt = &P.terms[t0 + k];
-      const float xh = (signed_ && k == 1) ? vh[1] : vh[0];
-      const float xl = (signed_ && k == 1) ? vl[1] : vl[0];
-      const bool neg = __popcll(base & __ldg(&tt->q)) & 1;
-      acc_scaled(th, tl, __ldg(&tt->kh), __ldg(&tt->kl), neg ? -xh : xh, neg ? -xl : xl);
+      const uint4 w = __ldg((const uint4*)&tt->kh);              // kh, kh2, kl, kl2
+      const uint64_t sb = (uint64_t)(__popcll(base & __ldg(&tt->q)) & 1) << 31;
+      const uint64_t s2 = sb | (sb << 32);                        // the tile's sign, both lanes
+      const uint64_t wh = ((uint64_t)w.x | ((uint64_t)w.y << 32)) ^ s2;
+      const uint64_t wl = ((uint64_t)w.z | ((uint64_t)w.w << 32)) ^ s2;
+      const bool second = signed_ && k == 1;
+      acc_w2(TH, TL, wh, wl, second ? vh[1] : vh[0], second ? vl[1] : vl[0], zz);
     }
   }
+}
+
+// complex128 component (IEEE double: low word w0, high word w1) -> hi + lo
+// floats holding its leading 24 and next 23 significand bits (truncated:
+// |x - (hi + lo)| < 2^-46 |x|).  |x| below 2^-100 (zero included) is first
+// raised to 2^-100 times its significand, sign kept: an absolute change below
+// 2^-99 per component, far under the sums' rounding.  |x| < 2^127.
+// Fewer instructions than the rounding, flushing split of the gate kernels;
+// in an expectation value the truncation costs at most
+// 2^-45 * ||psi||^2 * sum |c_t|.
+struct ffp { float h, l; };
+__device__ __forceinline__ ffp split_tr(uint32_t w0, uint32_t w1) {
+  const uint32_t mag = max(w1 & 0x7FFFFFFFu, 0x39B00000u);                 // exponent >= -100
+  // rebias the exponent (1023 -> 127), keep 23 mantissa bits; bit 31 of the
+  // shifted word is zero for |x| < 2^127, so the sign is or-ed in
+  const uint32_t hb = __funnelshift_l(w0, mag - 0x38000000u, 3) | (w1 & 0x80000000u);
+  // lo = (b + m) - b with b = +-2^(E-23) (hi's sign and exponent E) and m the
+  // next 23 bits (w0 bits 28..6) in b's mantissa field: exact
+  const uint32_t b = (hb & 0xFF800000u) - 0x0B800000u;
+  const uint32_t lb = b | ((w0 >> 6) & 0x007FFFFFu);
+  return {__uint_as_float(hb), __uint_as_float(lb) - __uint_as_float(b)};
 }
 
 // Load the 16 register amplitudes of arrangement a (complex128: the split form
@@ -695,8 +733,8 @@ __device__ __forceinline__ void reg_load(const unsigned char* tile, int a, uint3
     if constexpr (C128) {
       const uint4 v = *(const uint4*)(tile + (size_t)rslot<true>(l) * 16);
       if constexpr (RAW) {
-        const ArC128x::ff re = ArC128x::split(v.x, v.y);
-        const ArC128x::ff im = ArC128x::split(v.z, v.w);
+        const ffp re = split_tr(v.x, v.y);
+        const ffp im = split_tr(v.z, v.w);
         ah[r] = P2::pk(re.h, im.h);
         al[r] = P2::pk(re.l, im.l);
       } else {
@@ -710,108 +748,208 @@ __device__ __forceinline__ void reg_load(const unsigned char* tile, int a, uint3
   }
 }
 
+// three-input maximum (sm_100 and later)
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 // largest |component| (hi parts) of the 16 register amplitudes
 __device__ __forceinline__ float reg_max(const uint64_t* ah) {
   float m = 0.f;
 #pragma unroll
-  for (int r = 0; r < 16; r++) m = fmaxf(m, fmaxf(fabsf(P2::lo32(ah[r])), fabsf(P2::hi32(ah[r]))));
+  for (int r = 0; r < 16; r++) m = fmax3(m, fabsf(P2::lo32(ah[r])), fabsf(P2::hi32(ah[r])));
   return m;
 }
 
 // CTAs per SM of k_pauli_reg (its register bound: 128 / 85 registers a thread)
 constexpr int reg_ctas_per_sm(bool c128) { return c128 ? 2 : 3; }
 
+// Tiles of the register-resident kernel: 3 low bits, 9 generators.
+constexpr int kRegM = 3;
+constexpr int kRegH = kRegL - kRegM;
+// Diagonal terms with QL != 0 whose base-signed weights a tile stages in
+// shared memory (further ones take their sign and weight per thread).
+constexpr int kRegDiagSmem = 256;
+
+// Per-tile values staged in shared memory by warp 0.
+struct RegMisc {
+  uint64_t base[2];                // tile bases, double-buffered (next tile's written during this one)
+  float kh, kl;                    // sum over the QL = 0 diagonal terms of c_t (-1)^popc(base & Q_t)
+  uint32_t pad[2];
+};
+struct RegDiag {                   // a QL != 0 diagonal term, weight signed by the tile base
+  float kh, kl;
+  uint32_t ql, pad;
+};
+
+// Index of the first amplitude of tile tix: tix << m with zeros inserted at
+// the generators' pivot bits (ascending).
+__device__ __forceinline__ uint64_t tile_base(const TPass& P, uint64_t tix) {
+  uint64_t b = tix << P.m;
+  for (int i = 0; i < P.h; i++) b = qc_insert_zero(b, P.piv[i]);
+  return b;
+}
+
 template <bool C128>
 __global__ void __launch_bounds__(kTileThreads, reg_ctas_per_sm(C128))
 k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass P, double* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char rsm[];
   constexpr uint32_t kChunks = C128 ? (1u << kRegL) : (1u << (kRegL - 1));   // 16-byte chunks per tile
+  constexpr uint32_t kG = C128 ? 16u : 8u;                                    // state bytes per amplitude
+  constexpr int kNC = (int)(kChunks / kTileThreads);                         // chunks per thread
   unsigned char* tile = rsm;
-  uint64_t* gtab = (uint64_t*)(rsm + (size_t)kChunks * 16);
-  for (int c = threadIdx.x; c < (1 << P.h); c += kTileThreads) {
-    uint64_t g = 0;
-    for (int i = 0; i < P.h; i++)
-      if ((c >> i) & 1) g ^= P.gen[i];
-    gtab[c] = g;
-  }
-  const uint64_t zz = P.ntiles >> 63;
+  uint64_t* gtab = (uint64_t*)(rsm + (size_t)kChunks * 16);   // byte offsets of the generator combinations
+  RegMisc* misc = (RegMisc*)(gtab + (1 << kRegH));
+  RegDiag* drec = (RegDiag*)(misc + 1);
   const uint32_t t = threadIdx.x;
-  const uint32_t lowm = (1u << P.m) - 1u;
+  for (int c = (int)t; c < (1 << kRegH); c += kTileThreads) {
+    uint64_t g = 0;
+    for (int i = 0; i < kRegH; i++)
+      if ((c >> i) & 1) g ^= P.gen[i];
+    gtab[c] = g * kG;
+  }
+  if (t == 0) misc->base[0] = tile_base(P, blockIdx.x);
+  const uint64_t zz = P.ntiles >> 63;
   const uint32_t lb0 = t << 4;                                   // arrangement 0: bits [0, 4) in registers
   const uint32_t lb1 = (t & 15u) | ((t >> 4) << 8);              // arrangement 1: bits [4, 8)
   const uint32_t lb2 = t & 255u;                                 // arrangement 2: bits [8, 12)
-  double tot = 0.0;
-  for (uint64_t tix = blockIdx.x; tix < P.ntiles; tix += gridDim.x) {
-    float th = 0.f, tl = 0.f;
-    uint64_t base = tix << P.m;
-    for (int i = 0; i < P.h; i++) base = qc_insert_zero(base, P.piv[i]);
-    __syncthreads();                 // previous tile consumed, gtab written
-    {
-      // raw amplitudes, 16-byte cp.async chunks into their swizzled slots
-      constexpr uint32_t CA = C128 ? 1u : 2u;                   // amplitudes per chunk
-      const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tile);
-      for (uint32_t v = t; v < kChunks; v += kTileThreads) {
-        const uint32_t l = v * CA;
-        const uint64_t y = (base ^ gtab[l >> P.m]) + (l & lowm);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                     :: "r"(sbase + rslot<C128>(l) * 16u), "l"(psi + y * (C128 ? 16 : 8)) : "memory");
-      }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
+  // Tile copy: this thread's chunk i is chunk v = t + 256 i of the tile, local
+  // amplitude l = v (complex128) or 2 v (complex64): generator combination
+  // l >> 3 = gi0 + kGiStep * i, low bits l & 7 (lowb in bytes), swizzled slot
+  // rslot(l) = (t ^ s) + 256 i with s = (l >> 4) & 7, which depends on t only.
+  const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(tile) +
+                        16u * (C128 ? (t ^ ((t >> 4) & 7u)) : (t ^ ((t >> 3) & 7u)));
+  const uint32_t gi0 = C128 ? (t >> 3) : (t >> 2);
+  constexpr uint32_t kGiStep = C128 ? 32u : 64u;
+  const uint64_t lowb = C128 ? (uint64_t)((t & 7u) * 16u) : (uint64_t)((t & 3u) * 16u);
+  const int dthr = P.dnt - P.dtile;                              // diagonal terms with QL != 0
+  const int dsm = dthr < kRegDiagSmem ? dthr : kRegDiagSmem;
+  // raw amplitudes of the tile at `base`, 16-byte cp.async chunks into their
+  // swizzled slots; base and the generator combinations have no bits below
+  // bit 3, so the byte offset is (base ^ G) * kG | low bytes
+  auto copy_tile = [&](uint64_t base) {
+    const uint64_t baseb = base * kG;
+#pragma unroll
+    for (int i = 0; i < kNC; i++) {
+      const uint64_t off = (baseb ^ gtab[gi0 + kGiStep * (uint32_t)i]) | lowb;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                   :: "r"(sdst + 4096u * (uint32_t)i), "l"(psi + off) : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  double tot = 0.0;
+  int kb = 0;
+  for (uint64_t tix = blockIdx.x; tix < P.ntiles; tix += gridDim.x, kb ^= 1) {
+    __syncthreads();                 // previous tile consumed; gtab and this tile's base written
+    const uint64_t base = misc->base[kb];
+    copy_tile(base);
+    const bool next = tix + gridDim.x < P.ntiles;
+    if (t < 32) {
+      // warp 0, while the copies are in flight: the next tile's base and the
+      // diagonal terms' tile signs
+      if (t == 0 && next) misc->base[kb ^ 1] = tile_base(P, tix + gridDim.x);
+      if (P.dtile > 0) {
+        // sum of c_t (-1)^popc(base & Q_t) over the QL = 0 terms, float-float
+        float kh = 0.f, kl = 0.f;
+        for (int j = (int)t; j < P.dtile; j += 32) {
+          const TTerm* tt = &P.terms[P.dt0 + j];
+          const uint32_t sb = (uint32_t)(__popcll(base & __ldg(&tt->q)) & 1) << 31;
+          float s, e;
+          two_sum(kh, __uint_as_float(__float_as_uint(__ldg(&tt->kh)) ^ sb), s, e);
+          kh = s;
+          kl = __fadd_rn(kl, __fadd_rn(e, __uint_as_float(__float_as_uint(__ldg(&tt->kl)) ^ sb)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oh = __shfl_xor_sync(0xFFFFFFFFu, kh, o), ol = __shfl_xor_sync(0xFFFFFFFFu, kl, o);
+          float s, e;
+          two_sum(kh, oh, s, e);
+          kh = s;
+          kl = __fadd_rn(kl, __fadd_rn(ol, e));
+        }
+        if (t == 0) { misc->kh = kh; misc->kl = kl; }
+      }
+      for (int j = (int)t; j < dsm; j += 32) {
+        const TTerm* tt = &P.terms[P.dt0 + P.dtile + j];
+        const uint32_t sb = (uint32_t)(__popcll(base & __ldg(&tt->q)) & 1) << 31;
+        RegDiag d;
+        d.kh = __uint_as_float(__float_as_uint(__ldg(&tt->kh)) ^ sb);
+        d.kl = __uint_as_float(__float_as_uint(__ldg(&tt->kl)) ^ sb);
+        d.ql = __ldg(&tt->ql);
+        d.pad = 0u;
+        drec[j] = d;
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     uint64_t ah[16], al[16];
+    uint64_t TH = 0ull, TL = 0ull;   // pair terms, packed float-float; the lanes are added per tile
+    float th = 0.f, tl = 0.f;        // diagonal terms and the shared-memory groups
     // arrangement 0: raw -> split in registers, pair groups, diagonal terms, split form back
     reg_load<C128, true>(tile, 0, lb0, ah, al);
-    if (P.garr[1] > P.garr[0])
-      reg_groups<C128>(P, P.garr[0], P.garr[1], 0, lb0, base, ah, al, chain_sigma(reg_max(ah)), th, tl);
+    const uint64_t sig0 = chain_sigma(reg_max(ah));
+    if (P.garr[1] > P.garr[0]) reg_groups<C128>(P, P.garr[0], P.garr[1], 0, lb0, base, ah, al, sig0, zz, TH, TL);
     unsigned char* own = tile + (size_t)(C128 ? lb0 : (lb0 >> 1)) * 16;   // this thread's 16 amplitudes' chunks
     if (P.dnt > 0) {
-      // |psi|^2 of the 16 amplitudes, Walsh-Hadamard transform over the register bits
-      float ph[16], pl[16];
+      // |psi|^2 of the 16 amplitudes on the fixed grid of sigma: per lane
+      // hi = fma(a, a, sigma) - sigma is exact, a multiple of ulp(sigma) =
+      // 2^(E-23), and lo = the square's remainder (+ complex128's 2 hi*lo).
+      // The lanes' hi add exactly, and so does every Walsh-Hadamard sum of
+      // them (at most 32 mx^2 + 16 ulp <= 2^(E+1) = 2^24 ulp); lo adds in FP32.
+      float wh[16], wl[16];
 #pragma unroll
       for (int k = 0; k < 16; k++) {
-        const uint64_t p = prod2(ah[k], ah[k], zz);
-        uint64_t e = P2::fma2(ah[k], ah[k], neg2(p));          // hi*hi exact
-        if constexpr (C128) e = P2::add2(e, P2::mul2(P2::add2(ah[k], ah[k]), al[k]));
-        float s2, r2;
-        two_sum(P2::lo32(p), P2::hi32(p), s2, r2);
-        ph[k] = s2;
-        pl[k] = __fadd_rn(r2, __fadd_rn(P2::lo32(e), P2::hi32(e)));
+        const uint64_t t1 = P2::fma2(ah[k], ah[k], sig0);
+        const uint64_t r = P2::fma2(ah[k], ah[k], P2::sub2(sig0, t1));
+        const uint64_t h2 = P2::sub2(t1, sig0);
+        const uint64_t l2 = C128 ? P2::fma2(P2::add2(ah[k], ah[k]), al[k], r) : r;
+        wh[k] = __fadd_rn(P2::lo32(h2), P2::hi32(h2));
+        wl[k] = __fadd_rn(P2::lo32(l2), P2::hi32(l2));
       }
 #pragma unroll
       for (int b = 1; b < 16; b <<= 1) {
 #pragma unroll
         for (int k = 0; k < 16; k++) {
           if (!(k & b)) {
-            const float xh = ph[k], xl = pl[k], yh = ph[k | b], yl = pl[k | b];
-            float s2, e2;
-            two_sum(xh, yh, s2, e2);
-            ph[k] = s2;
-            pl[k] = __fadd_rn(__fadd_rn(xl, yl), e2);
-            two_sum(xh, -yh, s2, e2);
-            ph[k | b] = s2;
-            pl[k | b] = __fadd_rn(__fsub_rn(xl, yl), e2);
+            const float xh = wh[k], yh = wh[k | b], xl = wl[k], yl = wl[k | b];
+            wh[k] = __fadd_rn(xh, yh);
+            wh[k | b] = __fsub_rn(xh, yh);
+            wl[k] = __fadd_rn(xl, yl);
+            wl[k | b] = __fsub_rn(xl, yl);
           }
         }
       }
-      // W[u] into this thread's own chunks, entry u at 8 (u ^ (lane & 15)) bytes:
-      // the 16 lanes of a wavefront use 16 different bank pairs
-      const uint32_t wsw = t & 15u;
+      // QL = 0 terms: the tile-signed weight sum staged by warp 0, times W[0]
+      if (P.dtile > 0) acc_scaled(th, tl, misc->kh, misc->kl, wh[0], wl[0]);
+      if (dthr > 0) {
+        // W[u] into this thread's own chunks, entry u at 8 (u ^ (lane & 15)) bytes:
+        // the 16 lanes of a wavefront use 16 different bank pairs
+        const uint32_t wsw = t & 15u;
 #pragma unroll
-      for (int k = 0; k < 16; k++) *(float2*)(own + 8 * ((uint32_t)k ^ wsw)) = make_float2(ph[k], pl[k]);
-      const uint64_t y0 = base ^ gtab[lb0 >> P.m] ^ (lb0 & lowm);
-      for (int ti = P.dt0; ti < P.dt0 + P.dnt; ti++) {
-        const TTerm* tt = &P.terms[ti];
-        const uint32_t u = __ldg(&tt->ql) & 15u;
-        const float2 w = *(const float2*)(own + 8 * (u ^ wsw));
-        const uint32_t sb = (uint32_t)__popcll(y0 & __ldg(&tt->q)) << 31;
-        acc_scaled(th, tl, __uint_as_float(__float_as_uint(__ldg(&tt->kh)) ^ sb),
-                   __uint_as_float(__float_as_uint(__ldg(&tt->kl)) ^ sb), w.x, w.y);
+        for (int k = 0; k < 16; k++) *(float2*)(own + 8 * ((uint32_t)k ^ wsw)) = make_float2(wh[k], wl[k]);
+        // a term's sign at the thread's amplitudes: the tile's (in the staged
+        // weight) times (-1)^popc(lb0 & QL); the register bits' part is in W[QL & 15]
+        for (int j = 0; j < dsm; j++) {
+          const RegDiag d = drec[j];
+          const float2 w = *(const float2*)(own + 8 * ((d.ql & 15u) ^ wsw));
+          const uint32_t sb = (uint32_t)(__popc(lb0 & d.ql) & 1) << 31;
+          acc_scaled(th, tl, __uint_as_float(__float_as_uint(d.kh) ^ sb), __uint_as_float(__float_as_uint(d.kl) ^ sb),
+                     w.x, w.y);
+        }
+        for (int j = dsm; j < dthr; j++) {
+          const TTerm* tt = &P.terms[P.dt0 + P.dtile + j];
+          const uint32_t ql = __ldg(&tt->ql);
+          const float2 w = *(const float2*)(own + 8 * ((ql & 15u) ^ wsw));
+          const uint32_t sb = (uint32_t)((__popcll(base & __ldg(&tt->q)) + __popc(lb0 & ql)) & 1) << 31;
+          acc_scaled(th, tl, __uint_as_float(__float_as_uint(__ldg(&tt->kh)) ^ sb),
+                     __uint_as_float(__float_as_uint(__ldg(&tt->kl)) ^ sb), w.x, w.y);
+        }
       }
     }
     const bool later = P.garr[3] > P.garr[1] || P.ngroups > P.garr[3];
-    if (later && (C128 || P.dnt > 0)) {
+    if (later && (C128 || dthr > 0)) {
       // the split form (complex128) or the amplitudes themselves (complex64) back into the own chunks
       if constexpr (C128) {
 #pragma unroll
@@ -830,11 +968,11 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
       __syncthreads();
       if (P.garr[2] > P.garr[1]) {
         reg_load<C128, false>(tile, 1, lb1, ah, al);
-        reg_groups<C128>(P, P.garr[1], P.garr[2], 1, lb1, base, ah, al, chain_sigma(reg_max(ah)), th, tl);
+        reg_groups<C128>(P, P.garr[1], P.garr[2], 1, lb1, base, ah, al, chain_sigma(reg_max(ah)), zz, TH, TL);
       }
       if (P.garr[3] > P.garr[2]) {
         reg_load<C128, false>(tile, 2, lb2, ah, al);
-        reg_groups<C128>(P, P.garr[2], P.garr[3], 2, lb2, base, ah, al, chain_sigma(reg_max(ah)), th, tl);
+        reg_groups<C128>(P, P.garr[2], P.garr[3], 2, lb2, base, ah, al, chain_sigma(reg_max(ah)), zz, TH, TL);
       }
       for (int gi = P.garr[3]; gi < P.ngroups; gi++) {
         TGroup g;
@@ -851,7 +989,14 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
         }
       }
     }
-    tot += ArC128x::f2d(th) + ArC128x::f2d(tl);
+    {
+      // the tile's sum: both lanes of (TH, TL) and (th, tl), then two exact conversions
+      float s, e, s2, e2;
+      two_sum(P2::lo32(TH), P2::hi32(TH), s, e);
+      two_sum(th, s, s2, e2);
+      const float l = __fadd_rn(__fadd_rn(tl, e2), __fadd_rn(e, __fadd_rn(P2::lo32(TL), P2::hi32(TL))));
+      tot += ArC128x::f2d(s2) + ArC128x::f2d(l);
+    }
   }
   const double bs = block_sum(tot);
   if (threadIdx.x == 0) partial[blockIdx.x] = bs;
@@ -1046,6 +1191,9 @@ int tile_plan(int n, bool c128, const std::vector<HTerm>& terms_in, TilePlan& pl
       x.pad = 0u;
       x.kh = (float)k;
       x.kl = (float)(k - (double)x.kh);
+      const bool im = pair && (t->ny & 1);
+      x.kh2 = im ? -x.kh : x.kh;
+      x.kl2 = im ? -x.kl : x.kl;
       plan.terms.push_back(x);
     };
     auto push_group = [&](uint32_t fl, uint32_t kind, const std::vector<const HTerm*>& v, size_t i0, size_t cnt) {
@@ -1086,8 +1234,13 @@ int tile_plan(int n, bool c128, const std::vector<HTerm>& terms_in, TilePlan& pl
         }
       }
     }
+    // diagonal terms: those whose phase mask misses the tile's bits (QL = 0) first
     P.dt0 = (int)plan.terms.size() - t_begin;
-    for (const HTerm* t : diag) push_term(t, false);
+    for (const HTerm* t : diag)
+      if (local_q(t->Q) == 0) push_term(t, false);
+    P.dtile = (int)plan.terms.size() - t_begin - P.dt0;
+    for (const HTerm* t : diag)
+      if (local_q(t->Q) != 0) push_term(t, false);
     P.dnt = (int)diag.size();
     P.ngroups = (int)plan.groups.size() - g_begin;
     plan.term_off.push_back(t_begin);
@@ -1117,12 +1270,16 @@ int get_tables(int device, size_t bytes, void** p) {
 template <bool C128>
 int launch_reg(const qc_state* s, const TPass& P, double* partial, int grid) {
   constexpr size_t kChunks = C128 ? ((size_t)1 << kRegL) : ((size_t)1 << (kRegL - 1));
-  const size_t smem = kChunks * 16 + ((size_t)8 << P.h);
+  constexpr size_t kFixed = kChunks * 16 + ((size_t)8 << kRegH) + sizeof(RegMisc);
+  if (P.m != kRegM || P.h != kRegH || P.L != kRegL)
+    return qc_fail(QC_ERR_ARG, "internal: register-resident pass with m=%d h=%d L=%d", P.m, P.h, P.L);
+  const int dthr = P.dnt - P.dtile;
+  const size_t smem = kFixed + sizeof(RegDiag) * (size_t)std::min(dthr, kRegDiagSmem);
   static bool attr[64] = {false};
   const int dev = s->device;
   if (dev < 0 || dev >= 64 || !attr[dev]) {
     QC_CUDA(cudaFuncSetAttribute(k_pauli_reg<C128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kChunks * 16 + (8 << kTileMaxH))));
+                                 (int)(kFixed + sizeof(RegDiag) * kRegDiagSmem)));
     QC_CUDA(cudaFuncSetAttribute(k_pauli_reg<C128>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared));
     if (dev >= 0 && dev < 64) attr[dev] = true;
