@@ -621,18 +621,6 @@ __device__ __forceinline__ void reg_pairs(const uint64_t* ah, const uint64_t* al
   }
 }
 
-template <bool C128, int FLR>
-__device__ __forceinline__ void reg_pairs_kind(uint32_t kind, const uint64_t* ah, const uint64_t* al, uint64_t sig,
-                                               const uint32_t* lsign, const uint32_t* qlr, int nt, uint64_t* vh,
-                                               uint64_t* vl) {
-  switch (kind) {
-    case 0: reg_pairs<C128, FLR, false, false>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
-    case 1: reg_pairs<C128, FLR, true, false>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
-    case 2: reg_pairs<C128, FLR, false, true>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
-    default: reg_pairs<C128, FLR, true, true>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
-  }
-}
-
 // Packed weighted accumulation, per lane: (TH, TL) += (wh + wl) * (xh + xl),
 // wh * xh exact (TwoProduct), the cross terms rounded once, the sum TwoSum.
 __device__ __forceinline__ void acc_w2(uint64_t& TH, uint64_t& TL, uint64_t wh, uint64_t wl, uint64_t xh, uint64_t xl,
@@ -642,34 +630,76 @@ __device__ __forceinline__ void acc_w2(uint64_t& TH, uint64_t& TL, uint64_t wh, 
   acc2(TH, TL, p, P2::fma2(wh, xl, P2::fma2(wl, xh, e)));
 }
 
+// Pair groups staged in shared memory (the first kRegGroupSmem of a pass's
+// register-arrangement groups): the record once per CTA, the weights once
+// per tile (warp 0, while the tile copy is in flight).
+constexpr int kRegGroupSmem = 128;
+struct RegGroup {
+  uint32_t fl, kind;
+  int t0, nt;
+  uint32_t ql0, ql1;               // the local phase masks of a signed group's (at most two) terms
+  uint32_t pad[2];
+};
+struct RegGW {                     // packed weights (hi, lo), each lane pair (k, +-k)
+  uint64_t wh0, wl0;               // unsigned group: sum_t c_t (-1)^popc(base & Q_t); signed: term 0's
+  uint64_t wh1, wl1;               // signed group: term 1's
+};
+
+// Packed weights of term t, its sign (-1)^popc(base & Q_t) applied.
+__device__ __forceinline__ void term_w2(const TTerm* tt, uint64_t base, uint64_t& wh, uint64_t& wl) {
+  const uint4 w = __ldg((const uint4*)&tt->kh);                  // kh, kh2, kl, kl2
+  const uint64_t sb = (uint64_t)(__popcll(base & __ldg(&tt->q)) & 1) << 31;
+  const uint64_t s2 = sb | (sb << 32);
+  wh = ((uint64_t)w.x | ((uint64_t)w.y << 32)) ^ s2;
+  wl = ((uint64_t)w.z | ((uint64_t)w.w << 32)) ^ s2;
+}
+
 // The groups [g0, g1) of arrangement `a` (register bits [4a, 4a + 4)) for this
 // thread's registers; lbase = the thread's local index with zero register bits.
-// Each term adds its packed weight times the group's packed lane sums to the
-// packed accumulator (TH, TL); the lanes are added once per tile.
+// Each term (an unsigned group: its terms' summed weight) adds its packed
+// weight times the group's packed lane sums to the packed accumulator
+// (TH, TL); the lanes are added once per tile.
 template <bool C128>
-__device__ __forceinline__ void reg_groups(const TPass& P, int g0, int g1, int a, uint32_t lbase, uint64_t base,
-                                           const uint64_t* ah, const uint64_t* al, uint64_t sig, uint64_t zz,
-                                           uint64_t& TH, uint64_t& TL) {
+__device__ __forceinline__ void reg_groups(const TPass& P, const RegGroup* sg, const RegGW* sw, int g0, int g1, int a,
+                                           uint32_t lbase, uint64_t base, const uint64_t* ah, const uint64_t* al,
+                                           uint64_t sig, uint64_t zz, uint64_t& TH, uint64_t& TL) {
   for (int gi = g0; gi < g1; gi++) {
-    const uint32_t fl = __ldg(&P.groups[gi].fl);
-    const int t0 = __ldg(&P.groups[gi].t0);
-    const int nt = __ldg(&P.groups[gi].nt);
-    const uint32_t kind = __ldg(&P.groups[gi].kind);
+    const bool staged = gi < kRegGroupSmem;
+    uint32_t fl, kind, ql0 = 0u, ql1 = 0u;
+    int t0, nt;
+    if (staged) {
+      const uint4 r = *(const uint4*)&sg[gi];
+      fl = r.x; kind = r.y; t0 = (int)r.z; nt = (int)r.w;
+      if (kind & 2u) {
+        const uint2 q = *(const uint2*)&sg[gi].ql0;
+        ql0 = q.x; ql1 = q.y;
+      }
+    } else {
+      fl = __ldg(&P.groups[gi].fl);
+      t0 = __ldg(&P.groups[gi].t0);
+      nt = __ldg(&P.groups[gi].nt);
+      kind = __ldg(&P.groups[gi].kind);
+      if (kind & 2u) {
+        ql0 = __ldg(&P.terms[t0].ql);
+        if (nt > 1) ql1 = __ldg(&P.terms[t0 + 1].ql);
+      }
+    }
     static_assert(kGroupTerms == 2, "two accumulators per signed group");
     uint32_t lsign[kGroupTerms] = {0u, 0u}, qlr[kGroupTerms] = {0u, 0u};
     if (kind & 2u) {
-      const uint32_t q0 = __ldg(&P.terms[t0].ql);
-      lsign[0] = (uint32_t)__popc(lbase & q0) & 1u;
-      qlr[0] = (q0 >> (4 * a)) & 15u;
-      if (nt > 1) {
-        const uint32_t q1 = __ldg(&P.terms[t0 + 1].ql);
-        lsign[1] = (uint32_t)__popc(lbase & q1) & 1u;
-        qlr[1] = (q1 >> (4 * a)) & 15u;
-      }
+      lsign[0] = (uint32_t)__popc(lbase & ql0) & 1u;
+      qlr[0] = (ql0 >> (4 * a)) & 15u;
+      lsign[1] = (uint32_t)__popc(lbase & ql1) & 1u;
+      qlr[1] = (ql1 >> (4 * a)) & 15u;
     }
     uint64_t vh[kGroupTerms] = {0ull, 0ull}, vl[kGroupTerms] = {0ull, 0ull};
-    switch ((fl >> (4 * a)) & 15u) {
-#define QC_REG_CASE(F) case F: reg_pairs_kind<C128, F>(kind, ah, al, sig, lsign, qlr, nt, vh, vl); break;
+    // one jump on (flip mask in the register bits, kind)
+    switch ((((fl >> (4 * a)) & 15u) << 2) | kind) {
+#define QC_REG_CASE(F)                                                                                 \
+  case 4 * F + 0: reg_pairs<C128, F, false, false>(ah, al, sig, lsign, qlr, nt, vh, vl); break;      \
+  case 4 * F + 1: reg_pairs<C128, F, true, false>(ah, al, sig, lsign, qlr, nt, vh, vl); break;       \
+  case 4 * F + 2: reg_pairs<C128, F, false, true>(ah, al, sig, lsign, qlr, nt, vh, vl); break;       \
+  case 4 * F + 3: reg_pairs<C128, F, true, true>(ah, al, sig, lsign, qlr, nt, vh, vl); break;
       QC_REG_CASE(1) QC_REG_CASE(2) QC_REG_CASE(3) QC_REG_CASE(4) QC_REG_CASE(5) QC_REG_CASE(6) QC_REG_CASE(7)
       QC_REG_CASE(8) QC_REG_CASE(9) QC_REG_CASE(10) QC_REG_CASE(11) QC_REG_CASE(12) QC_REG_CASE(13)
       QC_REG_CASE(14) QC_REG_CASE(15)
@@ -677,15 +707,22 @@ __device__ __forceinline__ void reg_groups(const TPass& P, int g0, int g1, int a
       default: break;
     }
     const bool signed_ = (kind & 2u) != 0;
-    for (int k = 0; k < nt; k++) {
-      const TTerm* tt = &P.terms[t0 + k];
-      const uint4 w = __ldg((const uint4*)&tt->kh);              // kh, kh2, kl, kl2
-      const uint64_t sb = (uint64_t)(__popcll(base & __ldg(&tt->q)) & 1) << 31;
-      const uint64_t s2 = sb | (sb << 32);                        // the tile's sign, both lanes
-      const uint64_t wh = ((uint64_t)w.x | ((uint64_t)w.y << 32)) ^ s2;
-      const uint64_t wl = ((uint64_t)w.z | ((uint64_t)w.w << 32)) ^ s2;
-      const bool second = signed_ && k == 1;
-      acc_w2(TH, TL, wh, wl, second ? vh[1] : vh[0], second ? vl[1] : vl[0], zz);
+    if (staged) {
+      const RegGW* w = &sw[gi];
+      const uint4 w0 = *(const uint4*)&w->wh0;
+      acc_w2(TH, TL, (uint64_t)w0.x | ((uint64_t)w0.y << 32), (uint64_t)w0.z | ((uint64_t)w0.w << 32), vh[0], vl[0], zz);
+      if (signed_ && nt > 1) {
+        const uint4 w1 = *(const uint4*)&w->wh1;
+        acc_w2(TH, TL, (uint64_t)w1.x | ((uint64_t)w1.y << 32), (uint64_t)w1.z | ((uint64_t)w1.w << 32), vh[1], vl[1],
+               zz);
+      }
+    } else {
+      for (int k = 0; k < nt; k++) {
+        uint64_t wh, wl;
+        term_w2(&P.terms[t0 + k], base, wh, wl);
+        const bool second = signed_ && k == 1;
+        acc_w2(TH, TL, wh, wl, second ? vh[1] : vh[0], second ? vl[1] : vl[0], zz);
+      }
     }
   }
 }
@@ -802,8 +839,22 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
   unsigned char* tile = rsm;
   uint64_t* gtab = (uint64_t*)(rsm + (size_t)kChunks * 16);   // byte offsets of the generator combinations
   RegMisc* misc = (RegMisc*)(gtab + (1 << kRegH));
-  RegDiag* drec = (RegDiag*)(misc + 1);
+  const int ngs = P.garr[3] < kRegGroupSmem ? P.garr[3] : kRegGroupSmem;   // staged pair groups
+  RegGroup* sg = (RegGroup*)(misc + 1);
+  RegGW* sw = (RegGW*)(sg + ngs);
+  RegDiag* drec = (RegDiag*)(sw + ngs);
   const uint32_t t = threadIdx.x;
+  for (int gi = (int)t; gi < ngs; gi += kTileThreads) {
+    RegGroup g;
+    g.fl = __ldg(&P.groups[gi].fl);
+    g.kind = __ldg(&P.groups[gi].kind);
+    g.t0 = __ldg(&P.groups[gi].t0);
+    g.nt = __ldg(&P.groups[gi].nt);
+    g.ql0 = (g.kind & 2u) ? __ldg(&P.terms[g.t0].ql) : 0u;
+    g.ql1 = ((g.kind & 2u) && g.nt > 1) ? __ldg(&P.terms[g.t0 + 1].ql) : 0u;
+    g.pad[0] = g.pad[1] = 0u;
+    sg[gi] = g;
+  }
   for (int c = (int)t; c < (1 << kRegH); c += kTileThreads) {
     uint64_t g = 0;
     for (int i = 0; i < kRegH; i++)
@@ -871,6 +922,33 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
         }
         if (t == 0) { misc->kh = kh; misc->kl = kl; }
       }
+      // the staged pair groups' weights, signed by this tile's base
+      for (int gi = (int)t; gi < ngs; gi += 32) {
+        const int t0 = __ldg(&P.groups[gi].t0), nt = __ldg(&P.groups[gi].nt);
+        const uint32_t kind = __ldg(&P.groups[gi].kind);
+        RegGW w;
+        if (kind & 2u) {
+          term_w2(&P.terms[t0], base, w.wh0, w.wl0);
+          w.wh1 = w.wl1 = 0ull;
+          if (nt > 1) term_w2(&P.terms[t0 + 1], base, w.wh1, w.wl1);
+        } else {
+          // the group's terms share FL, the weight (Re or Im w) and QL = 0: one summed weight
+          float kh = 0.f, kl = 0.f;
+          for (int k = 0; k < nt; k++) {
+            const TTerm* tt = &P.terms[t0 + k];
+            const uint32_t sb = (uint32_t)(__popcll(base & __ldg(&tt->q)) & 1) << 31;
+            float s1, e1;
+            two_sum(kh, __uint_as_float(__float_as_uint(__ldg(&tt->kh)) ^ sb), s1, e1);
+            kh = s1;
+            kl = __fadd_rn(kl, __fadd_rn(e1, __uint_as_float(__float_as_uint(__ldg(&tt->kl)) ^ sb)));
+          }
+          const uint32_t im = (kind & 1u) << 31;               // Im w: the second lane's weight negated
+          w.wh0 = (uint64_t)__float_as_uint(kh) | ((uint64_t)(__float_as_uint(kh) ^ im) << 32);
+          w.wl0 = (uint64_t)__float_as_uint(kl) | ((uint64_t)(__float_as_uint(kl) ^ im) << 32);
+          w.wh1 = w.wl1 = 0ull;
+        }
+        sw[gi] = w;
+      }
       for (int j = (int)t; j < dsm; j += 32) {
         const TTerm* tt = &P.terms[P.dt0 + P.dtile + j];
         const uint32_t sb = (uint32_t)(__popcll(base & __ldg(&tt->q)) & 1) << 31;
@@ -890,7 +968,7 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
     // arrangement 0: raw -> split in registers, pair groups, diagonal terms, split form back
     reg_load<C128, true>(tile, 0, lb0, ah, al);
     const uint64_t sig0 = chain_sigma(reg_max(ah));
-    if (P.garr[1] > P.garr[0]) reg_groups<C128>(P, P.garr[0], P.garr[1], 0, lb0, base, ah, al, sig0, zz, TH, TL);
+    if (P.garr[1] > P.garr[0]) reg_groups<C128>(P, sg, sw, P.garr[0], P.garr[1], 0, lb0, base, ah, al, sig0, zz, TH, TL);
     unsigned char* own = tile + (size_t)(C128 ? lb0 : (lb0 >> 1)) * 16;   // this thread's 16 amplitudes' chunks
     if (P.dnt > 0) {
       // |psi|^2 of the 16 amplitudes on the fixed grid of sigma: per lane
@@ -968,11 +1046,11 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
       __syncthreads();
       if (P.garr[2] > P.garr[1]) {
         reg_load<C128, false>(tile, 1, lb1, ah, al);
-        reg_groups<C128>(P, P.garr[1], P.garr[2], 1, lb1, base, ah, al, chain_sigma(reg_max(ah)), zz, TH, TL);
+        reg_groups<C128>(P, sg, sw, P.garr[1], P.garr[2], 1, lb1, base, ah, al, chain_sigma(reg_max(ah)), zz, TH, TL);
       }
       if (P.garr[3] > P.garr[2]) {
         reg_load<C128, false>(tile, 2, lb2, ah, al);
-        reg_groups<C128>(P, P.garr[2], P.garr[3], 2, lb2, base, ah, al, chain_sigma(reg_max(ah)), zz, TH, TL);
+        reg_groups<C128>(P, sg, sw, P.garr[2], P.garr[3], 2, lb2, base, ah, al, chain_sigma(reg_max(ah)), zz, TH, TL);
       }
       for (int gi = P.garr[3]; gi < P.ngroups; gi++) {
         TGroup g;
@@ -1274,12 +1352,15 @@ int launch_reg(const qc_state* s, const TPass& P, double* partial, int grid) {
   if (P.m != kRegM || P.h != kRegH || P.L != kRegL)
     return qc_fail(QC_ERR_ARG, "internal: register-resident pass with m=%d h=%d L=%d", P.m, P.h, P.L);
   const int dthr = P.dnt - P.dtile;
-  const size_t smem = kFixed + sizeof(RegDiag) * (size_t)std::min(dthr, kRegDiagSmem);
+  const int ngs = std::min(P.garr[3], kRegGroupSmem);
+  const size_t smem = kFixed + (sizeof(RegGroup) + sizeof(RegGW)) * (size_t)ngs +
+                      sizeof(RegDiag) * (size_t)std::min(dthr, kRegDiagSmem);
   static bool attr[64] = {false};
   const int dev = s->device;
   if (dev < 0 || dev >= 64 || !attr[dev]) {
     QC_CUDA(cudaFuncSetAttribute(k_pauli_reg<C128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kFixed + sizeof(RegDiag) * kRegDiagSmem)));
+                                 (int)(kFixed + (sizeof(RegGroup) + sizeof(RegGW)) * kRegGroupSmem +
+                                       sizeof(RegDiag) * kRegDiagSmem)));
     QC_CUDA(cudaFuncSetAttribute(k_pauli_reg<C128>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared));
     if (dev >= 0 && dev < 64) attr[dev] = true;

@@ -104,6 +104,35 @@ def test_many_terms_share_a_flip_mask(q, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_more_register_groups_than_staged(q, dtype):
+    """n=13, one pass: every flip mask inside each 4-bit register window
+    (index bits 4a .. 4a+3, a = 0, 1, 2), each with three groups -- X only
+    plus the same X times Z on the global bit 12 (one unsigned group of two
+    terms whose signs differ between the two tiles), X times Z on two tile
+    bits outside the flip (one signed group of two terms), and a Y on the
+    lowest flip bit (an Im-weighted signed group): 135 pair groups, more than
+    the 128 whose records and weights a tile stages in shared memory."""
+    n = 13
+    qubit = lambda b: n - 1 - b            # qubit whose index bit is b
+    rng = np.random.default_rng(33)
+    H = []
+    for a in range(3):
+        for f in range(1, 16):
+            bits = [4 * a + b for b in range(4) if (f >> b) & 1]
+            xs = [("X", qubit(b)) for b in bits]
+            free = [b for b in range(12) if b not in bits]
+            z1, z2 = (int(b) for b in rng.choice(free, size=2, replace=False))
+            c = rng.uniform(-1, 1, size=5)
+            H.append((float(c[0]), xs))
+            H.append((float(c[1]), xs + [("Z", qubit(12))]))
+            H.append((float(c[2]), xs + [("Z", qubit(z1))]))
+            H.append((float(c[3]), xs + [("Z", qubit(z2))]))
+            H.append((float(c[4]), [("Y", qubit(bits[0]))] + xs[1:]))
+    assert q.expect_passes(n, q.C128 if dtype == "c128" else q.C64, H) == 1
+    check(q, n, dtype, H, seed=41)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_hamiltonian_families(q, dtype):
     n = 14
     heis = []
