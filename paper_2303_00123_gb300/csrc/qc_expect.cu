@@ -194,6 +194,8 @@ struct TPass {                     // kernel parameter: one pass
   uint64_t gen[kTileMaxH];         // generator masks
   int garr[4];                     // register-resident kernel: groups [garr[a], garr[a+1]) (a < 3;
                                    // garr[3] .. ngroups: from shared memory) use arrangement a
+  int qmask;                       // bit 4a + b: arrangement a's groups start with the Re-weighted,
+                                   // unsigned group of the single register bit b (in order of b)
   int reg;                         // 1: k_pauli_reg (tiles of 2^12), 0: k_pauli_tile
 };
 
@@ -663,7 +665,46 @@ template <bool C128>
 __device__ __forceinline__ void reg_groups(const TPass& P, const RegGroup* sg, const RegGW* sw, int g0, int g1, int a,
                                            uint32_t lbase, uint64_t base, const uint64_t* ah, const uint64_t* al,
                                            uint64_t sig, uint64_t zz, uint64_t& TH, uint64_t& TL) {
-  for (int gi = g0; gi < g1; gi++) {
+  // weight of an unsigned group (staged, or summed from its terms) times its lane sums
+  auto weigh = [&](int gi, uint64_t xh, uint64_t xl) {
+    if (gi < kRegGroupSmem) {
+      const uint4 w0 = *(const uint4*)&sw[gi].wh0;
+      acc_w2(TH, TL, (uint64_t)w0.x | ((uint64_t)w0.y << 32), (uint64_t)w0.z | ((uint64_t)w0.w << 32), xh, xl, zz);
+    } else {
+      const int t0 = __ldg(&P.groups[gi].t0), nt = __ldg(&P.groups[gi].nt);
+      for (int k = 0; k < nt; k++) {
+        uint64_t wh, wl;
+        term_w2(&P.terms[t0 + k], base, wh, wl);
+        acc_w2(TH, TL, wh, wl, xh, xl, zz);
+      }
+    }
+  };
+  // The arrangement's Re-weighted unsigned groups of single register bits
+  // (X or Y on one qubit, ...) come first: no dispatch, and with all four
+  // present one straight run of four chains that the compiler interleaves.
+  const uint32_t qm = ((uint32_t)P.qmask >> (4 * a)) & 15u;
+  int g = g0;
+  if (qm == 15u) {
+    const uint32_t z2[2] = {0u, 0u};
+    uint64_t h1[2], l1[2], h2[2], l2[2], h4[2], l4[2], h8[2], l8[2];
+    reg_pairs<C128, 1, false, false>(ah, al, sig, z2, z2, 1, h1, l1);
+    reg_pairs<C128, 2, false, false>(ah, al, sig, z2, z2, 1, h2, l2);
+    reg_pairs<C128, 4, false, false>(ah, al, sig, z2, z2, 1, h4, l4);
+    reg_pairs<C128, 8, false, false>(ah, al, sig, z2, z2, 1, h8, l8);
+    weigh(g, h1[0], l1[0]);
+    weigh(g + 1, h2[0], l2[0]);
+    weigh(g + 2, h4[0], l4[0]);
+    weigh(g + 3, h8[0], l8[0]);
+    g += 4;
+  } else if (qm) {
+    const uint32_t z2[2] = {0u, 0u};
+    uint64_t vh1[2], vl1[2];
+    if (qm & 1u) { reg_pairs<C128, 1, false, false>(ah, al, sig, z2, z2, 1, vh1, vl1); weigh(g++, vh1[0], vl1[0]); }
+    if (qm & 2u) { reg_pairs<C128, 2, false, false>(ah, al, sig, z2, z2, 1, vh1, vl1); weigh(g++, vh1[0], vl1[0]); }
+    if (qm & 4u) { reg_pairs<C128, 4, false, false>(ah, al, sig, z2, z2, 1, vh1, vl1); weigh(g++, vh1[0], vl1[0]); }
+    if (qm & 8u) { reg_pairs<C128, 8, false, false>(ah, al, sig, z2, z2, 1, vh1, vl1); weigh(g++, vh1[0], vl1[0]); }
+  }
+  for (int gi = g; gi < g1; gi++) {
     const bool staged = gi < kRegGroupSmem;
     uint32_t fl, kind, ql0 = 0u, ql1 = 0u;
     int t0, nt;
@@ -1293,8 +1334,16 @@ int tile_plan(int n, bool c128, const std::vector<HTerm>& terms_in, TilePlan& pl
         if ((fl & ~(15u << (4 * a))) == 0) return a;
       return 3;
     };
+    P.qmask = 0;
     for (int a = 0; a < 4; a++) {
       P.garr[a] = (int)plan.groups.size() - g_begin;
+      // an arrangement's Re-weighted unsigned groups of a single register bit
+      // come first, in order of the bit (the kernel runs them without dispatch)
+      auto single = [&](uint32_t fl) {
+        const uint32_t r = a < 3 ? fl >> (4 * a) : 0u;
+        return a < 3 && r != 0 && (r & (r - 1)) == 0;
+      };
+      for (int pass2 = 0; pass2 < 2; pass2++)
       for (auto& kv : by_fl) {
         if (arrangement(kv.first) != a) continue;
         // split by Re / Im weight and by whether the phase mask reaches into the tile
@@ -1303,6 +1352,9 @@ int tile_plan(int n, bool c128, const std::vector<HTerm>& terms_in, TilePlan& pl
         for (uint32_t kind = 0; kind < 4; kind++) {
           const std::vector<const HTerm*>& v = part[kind];
           if (v.empty()) continue;
+          const bool quad = kind == 0 && single(kv.first);
+          if (quad != (pass2 == 0)) continue;
+          if (quad) P.qmask |= (int)((kv.first >> (4 * a)) << (4 * a));
           if (kind & 2u) {
             for (size_t i = 0; i < v.size(); i += kGroupTerms)
               push_group(kv.first, kind, v, i, std::min<size_t>(kGroupTerms, v.size() - i));
