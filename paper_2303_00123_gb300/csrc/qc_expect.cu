@@ -834,11 +834,12 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
 }
 
 // largest |component| (hi parts) of the 16 register amplitudes
+// (four independent maxima, then combined: a quarter of the serial dependence)
 __device__ __forceinline__ float reg_max(const uint64_t* ah) {
-  float m = 0.f;
+  float m[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int r = 0; r < 16; r++) m = fmax3(m, fabsf(P2::lo32(ah[r])), fabsf(P2::hi32(ah[r])));
-  return m;
+  for (int r = 0; r < 16; r++) m[r & 3] = fmax3(m[r & 3], fabsf(P2::lo32(ah[r])), fabsf(P2::hi32(ah[r])));
+  return fmax3(fmaxf(m[0], m[1]), m[2], m[3]);
 }
 
 // CTAs per SM of k_pauli_reg (its register bound: 128 / 85 registers a thread)
@@ -1050,12 +1051,21 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
         for (int k = 0; k < 16; k++) *(float2*)(own + 8 * ((uint32_t)k ^ wsw)) = make_float2(wh[k], wl[k]);
         // a term's sign at the thread's amplitudes: the tile's (in the staged
         // weight) times (-1)^popc(lb0 & QL); the register bits' part is in W[QL & 15]
+        // two float-float accumulators on alternate terms: half the serial dependence
+        float uh = 0.f, ul = 0.f;
         for (int j = 0; j < dsm; j++) {
           const RegDiag d = drec[j];
           const float2 w = *(const float2*)(own + 8 * ((d.ql & 15u) ^ wsw));
           const uint32_t sb = (uint32_t)(__popc(lb0 & d.ql) & 1) << 31;
-          acc_scaled(th, tl, __uint_as_float(__float_as_uint(d.kh) ^ sb), __uint_as_float(__float_as_uint(d.kl) ^ sb),
-                     w.x, w.y);
+          const float kh = __uint_as_float(__float_as_uint(d.kh) ^ sb), kl = __uint_as_float(__float_as_uint(d.kl) ^ sb);
+          if (j & 1) acc_scaled(uh, ul, kh, kl, w.x, w.y);
+          else acc_scaled(th, tl, kh, kl, w.x, w.y);
+        }
+        {
+          float s1, e1;
+          two_sum(th, uh, s1, e1);
+          th = s1;
+          tl = __fadd_rn(tl, __fadd_rn(ul, e1));
         }
         for (int j = dsm; j < dthr; j++) {
           const TTerm* tt = &P.terms[P.dt0 + P.dtile + j];
