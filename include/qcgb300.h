@@ -416,7 +416,7 @@ int qc_expect_passes(int n, int dtype, const qc_pauli_sum* H, int* npasses);
  * Limit: at most 1023 sweeps, one per distinct X/Y pattern of the terms per
  * 64 terms; larger sums return QC_ERR_ARG before any work is enqueued.
  * The first call on a device looks the array's device address up (with that
- * device current); make that first call before any stream capture.  Every
+ * device current): the first call should come before any stream capture.  Every
  * call in the process uses the same array and leaves its own sums in it.
  * Calls whose work overlapped on the GPU would race on it; the library
  * prevents that within a process by serialising the calls -- each holds a
