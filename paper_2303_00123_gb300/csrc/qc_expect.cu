@@ -261,11 +261,19 @@ template <> struct TileT<false> {
   }
 };
 
-// Swizzled tile layout of the register-resident kernel (below): local
-// amplitude l lives in the 16-byte chunk c ^ ((l >> 4) & 7), c = l for
-// complex128 (one amplitude per chunk) and c = l >> 1 for complex64 (two).
+// Padded tile layout of the register-resident kernel (below): 16-byte chunk
+// c -- amplitude c (complex128) or amplitudes 2c, 2c + 1 (complex64) -- at
+// slot c + (c >> 4) (complex128) or c + (c >> 3) (complex64), one spare chunk
+// after every 16 (8).  The copy-in, the three arrangements' loads, the
+// write-back and the diagonal scratch then touch distinct banks across the
+// lanes of a wavefront, and each arrangement's 16 slots of a thread lie at
+// constant offsets from a per-thread base (reg_base, reg_stride).
 template <bool C128>
-__device__ __forceinline__ uint32_t rslot(uint32_t l) { return (C128 ? l : (l >> 1)) ^ ((l >> 4) & 7u); }
+__device__ __forceinline__ uint32_t rslot(uint32_t l) {
+  const uint32_t c = C128 ? l : (l >> 1);
+  return c + (c >> (C128 ? 4 : 3));
+}
+constexpr uint32_t reg_slots(bool c128) { return c128 ? 4096u + 256u : 2048u + 256u; }   // 16-byte slots per tile
 
 template <bool C128, bool SWZ>
 __device__ __forceinline__ typename TileT<C128>::amp tile_get(const unsigned char* t, uint32_t l) {
@@ -789,27 +797,49 @@ __device__ __forceinline__ ffp split_tr(uint32_t w0, uint32_t w1) {
   return {__uint_as_float(hb), __uint_as_float(lb) - __uint_as_float(b)};
 }
 
+// Byte offset of thread t's first amplitude of arrangement a in the padded
+// tile, and the step between its 16 amplitudes (register bit r at base + r
+// stride; complex64 arrangement 0: chunk j of 8 at base + 16 j).
+//   complex128: a=0 slot 17t + r; a=1 (t & 15) + 272 (t >> 4) + 17r;
+//               a=2 t + (t >> 4) + 272r
+//   complex64 (slot of chunk l >> 1, 8 bytes per amplitude): a=0 9t + j;
+//               a=1 ((t & 15) >> 1) + 144 (t >> 4) + 9r; a=2 (t >> 1) + (t >> 4) + 144r
+template <bool C128>
+__device__ __forceinline__ uint32_t reg_base(int a, uint32_t t) {
+  if constexpr (C128) {
+    return 16u * (a == 0 ? 17u * t : a == 1 ? (t & 15u) + 272u * (t >> 4) : t + (t >> 4));
+  } else {
+    const uint32_t half = 8u * (t & 1u);
+    return a == 0 ? 144u * t
+                  : (a == 1 ? 16u * (((t & 15u) >> 1) + 144u * (t >> 4)) + half : 16u * ((t >> 1) + (t >> 4)) + half);
+  }
+}
+template <bool C128>
+constexpr uint32_t reg_stride(int a) {
+  return C128 ? (a == 0 ? 16u : a == 1 ? 272u : 4352u) : (a == 0 ? 16u : a == 1 ? 144u : 2304u);
+}
+
 // Load the 16 register amplitudes of arrangement a (complex128: the split form
 // (hi pair, lo pair) from shared memory; RAW: the raw doubles, split here).
 template <bool C128, bool RAW>
-__device__ __forceinline__ void reg_load(const unsigned char* tile, int a, uint32_t lbase, uint64_t* ah, uint64_t* al) {
+__device__ __forceinline__ void reg_load(const unsigned char* tile, int a, uint32_t t, uint64_t* ah, uint64_t* al) {
+  const unsigned char* b = tile + reg_base<C128>(a, t);
   if (!C128 && a == 0) {
     // complex64, register bits [0, 4): the thread's 8 chunks, 16 bytes each
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-      const uint32_t l = lbase | (uint32_t)(2 * k);
-      const uint4 v = *(const uint4*)(tile + (size_t)rslot<false>(l) * 16);
+      const uint4 v = *(const uint4*)(b + 16 * k);
       ah[2 * k] = (uint64_t)v.x | ((uint64_t)v.y << 32);
       ah[2 * k + 1] = (uint64_t)v.z | ((uint64_t)v.w << 32);
       al[2 * k] = al[2 * k + 1] = 0ull;
     }
     return;
   }
+  const uint32_t stp = a == 0 ? reg_stride<C128>(0) : a == 1 ? reg_stride<C128>(1) : reg_stride<C128>(2);
 #pragma unroll
   for (int r = 0; r < 16; r++) {
-    const uint32_t l = lbase | ((uint32_t)r << (4 * a));
     if constexpr (C128) {
-      const uint4 v = *(const uint4*)(tile + (size_t)rslot<true>(l) * 16);
+      const uint4 v = *(const uint4*)(b + stp * (uint32_t)r);
       if constexpr (RAW) {
         const ffp re = split_tr(v.x, v.y);
         const ffp im = split_tr(v.z, v.w);
@@ -820,7 +850,7 @@ __device__ __forceinline__ void reg_load(const unsigned char* tile, int a, uint3
         al[r] = (uint64_t)v.z | ((uint64_t)v.w << 32);
       }
     } else {
-      ah[r] = *(const uint64_t*)(tile + (size_t)rslot<false>(l) * 16 + (l & 1u) * 8);
+      ah[r] = *(const uint64_t*)(b + stp * (uint32_t)r);
       al[r] = 0ull;
     }
   }
@@ -879,7 +909,7 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
   constexpr uint32_t kG = C128 ? 16u : 8u;                                    // state bytes per amplitude
   constexpr int kNC = (int)(kChunks / kTileThreads);                         // chunks per thread
   unsigned char* tile = rsm;
-  uint64_t* gtab = (uint64_t*)(rsm + (size_t)kChunks * 16);   // byte offsets of the generator combinations
+  uint64_t* gtab = (uint64_t*)(rsm + (size_t)reg_slots(C128) * 16);   // byte offsets of the generator combinations
   RegMisc* misc = (RegMisc*)(gtab + (1 << kRegH));
   const int ngs = P.garr[3] < kRegGroupSmem ? P.garr[3] : kRegGroupSmem;   // staged pair groups
   RegGroup* sg = (RegGroup*)(misc + 1);
@@ -911,9 +941,10 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
   // Tile copy: this thread's chunk i is chunk v = t + 256 i of the tile, local
   // amplitude l = v (complex128) or 2 v (complex64): generator combination
   // l >> 3 = gi0 + kGiStep * i, low bits l & 7 (lowb in bytes), swizzled slot
-  // rslot(l) = (t ^ s) + 256 i with s = (l >> 4) & 7, which depends on t only.
-  const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(tile) +
-                        16u * (C128 ? (t ^ ((t >> 4) & 7u)) : (t ^ ((t >> 3) & 7u)));
+  // rslot = v + (v >> 4) = t + (t >> 4) + 272 i (complex128) or
+  // v + (v >> 3) = t + (t >> 3) + 288 i (complex64).
+  const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(tile) + 16u * (C128 ? t + (t >> 4) : t + (t >> 3));
+  constexpr uint32_t kDstStep = C128 ? 16u * 272u : 16u * 288u;
   const uint32_t gi0 = C128 ? (t >> 3) : (t >> 2);
   constexpr uint32_t kGiStep = C128 ? 32u : 64u;
   const uint64_t lowb = C128 ? (uint64_t)((t & 7u) * 16u) : (uint64_t)((t & 3u) * 16u);
@@ -928,7 +959,7 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
     for (int i = 0; i < kNC; i++) {
       const uint64_t off = (baseb ^ gtab[gi0 + kGiStep * (uint32_t)i]) | lowb;
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                   :: "r"(sdst + 4096u * (uint32_t)i), "l"(psi + off) : "memory");
+                   :: "r"(sdst + kDstStep * (uint32_t)i), "l"(psi + off) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
@@ -1008,10 +1039,10 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
     uint64_t TH = 0ull, TL = 0ull;   // pair terms, packed float-float; the lanes are added per tile
     float th = 0.f, tl = 0.f;        // diagonal terms and the shared-memory groups
     // arrangement 0: raw -> split in registers, pair groups, diagonal terms, split form back
-    reg_load<C128, true>(tile, 0, lb0, ah, al);
+    reg_load<C128, true>(tile, 0, t, ah, al);
     const uint64_t sig0 = chain_sigma(reg_max(ah));
     if (P.garr[1] > P.garr[0]) reg_groups<C128>(P, sg, sw, P.garr[0], P.garr[1], 0, lb0, base, ah, al, sig0, zz, TH, TL);
-    unsigned char* own = tile + (size_t)(C128 ? lb0 : (lb0 >> 1)) * 16;   // this thread's 16 amplitudes' chunks
+    unsigned char* own = tile + reg_base<C128>(0, t);   // this thread's 16 amplitudes' chunks (arrangement 0)
     if (P.dnt > 0) {
       // |psi|^2 of the 16 amplitudes on the fixed grid of sigma: per lane
       // hi = fma(a, a, sigma) - sigma is exact, a multiple of ulp(sigma) =
@@ -1083,12 +1114,12 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
       if constexpr (C128) {
 #pragma unroll
         for (int r = 0; r < 16; r++)
-          *(uint4*)(tile + (size_t)rslot<true>(lb0 | (uint32_t)r) * 16) =
+          *(uint4*)(own + 16 * r) =
               make_uint4((uint32_t)ah[r], (uint32_t)(ah[r] >> 32), (uint32_t)al[r], (uint32_t)(al[r] >> 32));
       } else {
 #pragma unroll
         for (int k = 0; k < 8; k++)
-          *(uint4*)(tile + (size_t)rslot<false>(lb0 | (uint32_t)(2 * k)) * 16) =
+          *(uint4*)(own + 16 * k) =
               make_uint4((uint32_t)ah[2 * k], (uint32_t)(ah[2 * k] >> 32), (uint32_t)ah[2 * k + 1],
                          (uint32_t)(ah[2 * k + 1] >> 32));
       }
@@ -1096,11 +1127,11 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
     if (later) {
       __syncthreads();
       if (P.garr[2] > P.garr[1]) {
-        reg_load<C128, false>(tile, 1, lb1, ah, al);
+        reg_load<C128, false>(tile, 1, t, ah, al);
         reg_groups<C128>(P, sg, sw, P.garr[1], P.garr[2], 1, lb1, base, ah, al, chain_sigma(reg_max(ah)), zz, TH, TL);
       }
       if (P.garr[3] > P.garr[2]) {
-        reg_load<C128, false>(tile, 2, lb2, ah, al);
+        reg_load<C128, false>(tile, 2, t, ah, al);
         reg_groups<C128>(P, sg, sw, P.garr[2], P.garr[3], 2, lb2, base, ah, al, chain_sigma(reg_max(ah)), zz, TH, TL);
       }
       for (int gi = P.garr[3]; gi < P.ngroups; gi++) {
@@ -1409,8 +1440,7 @@ int get_tables(int device, size_t bytes, void** p) {
 
 template <bool C128>
 int launch_reg(const qc_state* s, const TPass& P, double* partial, int grid) {
-  constexpr size_t kChunks = C128 ? ((size_t)1 << kRegL) : ((size_t)1 << (kRegL - 1));
-  constexpr size_t kFixed = kChunks * 16 + ((size_t)8 << kRegH) + sizeof(RegMisc);
+  constexpr size_t kFixed = (size_t)reg_slots(C128) * 16 + ((size_t)8 << kRegH) + sizeof(RegMisc);
   if (P.m != kRegM || P.h != kRegH || P.L != kRegL)
     return qc_fail(QC_ERR_ARG, "internal: register-resident pass with m=%d h=%d L=%d", P.m, P.h, P.L);
   const int dthr = P.dnt - P.dtile;
