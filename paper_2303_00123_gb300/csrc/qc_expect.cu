@@ -970,14 +970,17 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
     const uint64_t base = misc->base[kb];
     copy_tile(base);
     const bool next = tix + gridDim.x < P.ntiles;
-    if (t < 32) {
-      // warp 0, while the copies are in flight: the next tile's base and the
-      // diagonal terms' tile signs
-      if (t == 0 && next) misc->base[kb ^ 1] = tile_base(P, tix + gridDim.x);
+    // While the copies are in flight, three warps stage this tile's signs in
+    // parallel (each job's global loads are a dependent chain before the
+    // barrier below): warp 0 the next tile's base and the QL = 0 diagonal sum,
+    // warp 1 the pair groups' weights, warp 2 the other diagonal terms.
+    const uint32_t lane = t & 31u, wid = t >> 5;
+    if (wid == 0) {
+      if (lane == 0 && next) misc->base[kb ^ 1] = tile_base(P, tix + gridDim.x);
       if (P.dtile > 0) {
         // sum of c_t (-1)^popc(base & Q_t) over the QL = 0 terms, float-float
         float kh = 0.f, kl = 0.f;
-        for (int j = (int)t; j < P.dtile; j += 32) {
+        for (int j = (int)lane; j < P.dtile; j += 32) {
           const TTerm* tt = &P.terms[P.dt0 + j];
           const uint32_t sb = (uint32_t)(__popcll(base & __ldg(&tt->q)) & 1) << 31;
           float s, e;
@@ -993,10 +996,11 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
           kh = s;
           kl = __fadd_rn(kl, __fadd_rn(ol, e));
         }
-        if (t == 0) { misc->kh = kh; misc->kl = kl; }
+        if (lane == 0) { misc->kh = kh; misc->kl = kl; }
       }
+    } else if (wid == 1) {
       // the staged pair groups' weights, signed by this tile's base
-      for (int gi = (int)t; gi < ngs; gi += 32) {
+      for (int gi = (int)lane; gi < ngs; gi += 32) {
         const int t0 = __ldg(&P.groups[gi].t0), nt = __ldg(&P.groups[gi].nt);
         const uint32_t kind = __ldg(&P.groups[gi].kind);
         RegGW w;
@@ -1022,7 +1026,8 @@ k_pauli_reg(const unsigned char* __restrict__ psi, const __grid_constant__ TPass
         }
         sw[gi] = w;
       }
-      for (int j = (int)t; j < dsm; j += 32) {
+    } else if (wid == 2) {
+      for (int j = (int)lane; j < dsm; j += 32) {
         const TTerm* tt = &P.terms[P.dt0 + P.dtile + j];
         const uint32_t sb = (uint32_t)(__popcll(base & __ldg(&tt->q)) & 1) << 31;
         RegDiag d;
