@@ -379,14 +379,18 @@ typedef struct {
 /* *out = <psi| H |psi> (real part), copied to the host (synchronises the
  * state's stream); the state is not modified.  The terms are evaluated in
  * passes over tiles of the state (see qc_expect_passes).  complex128:
- * amplitudes split into float pairs (47 bits), products exact in their
- * hi*hi part, each thread's sum of a term's products over its share of a
- * tile accumulated without rounding error in a fixed-exponent chain (the
- * rounding remainders and hi*lo cross terms in a second word), float-float
- * across a tile's terms, FP64 across tiles -- about 1e-15 from the exact value
- * for O(1) coefficients.  complex64: the same arithmetic on the FP32
- * amplitudes as they are (their products are exact in two floats), so the
- * result is the expectation of the complex64 state to about 1e-13 * sum |c_t|.
+ * amplitudes split into float pairs (47 bits, truncated); each thread's sum of
+ * a pair term's products over its share of a tile accumulates in a
+ * fixed-exponent chain (hi*hi products added exactly to the high word, their
+ * rounding remainders -- exact to 2^-24 of themselves -- and the hi*lo cross
+ * terms in a second word); diagonal terms use |psi|^2 on the same fixed grid,
+ * whose Walsh-Hadamard sums are exact in the high word and FP32 in the low
+ * word; weights and the sum over a tile's terms in float-float, FP64 across
+ * tiles.  Observed: about 1e-15 from the exact value for O(1) coefficients
+ * (worst case, every rounding at its maximum and aligned: about
+ * 2^-35 * sum |c_t|).  complex64: the same arithmetic on the FP32 amplitudes
+ * as they are (their products are exact in two floats), so the result is the
+ * expectation of the complex64 state to about 1e-13 * sum |c_t|.
  * QC_ERR_TIMEOUT as described at qc_device_status.
  * Deterministic (fixed grid, fixed reduction order). */
 int qc_expect(const qc_state* s, const qc_pauli_sum* H, double* out);
